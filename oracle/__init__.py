@@ -1,0 +1,21 @@
+"""FP64 CPU oracle for the relativistic-beam EM PIC step (arXiv:1910.13529).
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
+reference that the CUDA path is checked against.  Only tests/,
+__graft_entry__.smoke() and bench.py's cpu_baseline / reference leg may import,
+call, link or execute anything here; the product package never does, and the
+two share no code.
+
+Modules:
+  pic_oracle.c  the PIC step in plain C loops (field advance, gather, Boris,
+                Esirkepov deposit, current correction, Gauss residual, window)
+  core.py       ctypes wrappers and the step driver (Sim)
+  fit.py        Appendix C coefficient fit, Sec. 3 current-correction kernel, CFL
+  kspace.py     Sec. 2-3 k-space integrals: self-force, kappa_r, on-axis E1,
+                Appendix D closed forms
+
+Pins (tests/test_oracle_*.py): plane-wave dispersion of Eq. wave, Gauss's law kept
+to round-off, Esirkepov continuity, Boris closed forms, dense-matrix brute force on
+8x8 grids, Table 1 re-fit, the self-force and kappa_r values of Sec. 2-3.
+Parity unpinned: the 5-pass filter is not defined in the paper and is not built.
+"""
