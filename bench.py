@@ -1,0 +1,334 @@
+"""Benchmark of the relativistic-beam EM PIC step on GB300.
+
+Workload: the 2D beam-in-plasma run -- grid 2048 (z) x 512 (x), dz = dx = 0.02 c/omega_p,
+dt = 0.9 x the customised-stencil stability limit, moving window at c, bi-Gaussian electron
+beam (sigma_z = 0.5, sigma_x = 0.2, gamma = 2e4 with 2% spread, 1e6 macro-particles) in a
+uniform plasma of 4 particles per cell, quadratic shapes, customised M = 16 axial stencil,
+FP32 fields and offsets; particles sorted by cell every 20 steps.  One step = gather + Boris
++ Esirkepov deposition (fused) for both species, current correction, field advance, window
+shift / injection when due.
+
+Reported: particle-pushes/s for the whole step (value), cell-updates/s, the HBM roofline of
+the dominant kernel (the fused particle kernel), an end-to-end number through the C ABI from
+pinned host buffers, and the FP64 oracle timed on the host cores (cpu_baseline).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torch.distributed.run, one independent replica per GPU (weak scaling,
+no collective on the data path).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+BYTES_PER_PUSH_2D = 48          # read + write cell (4) + offsets (2 x 4) + u (3 x 4)
+BYTES_PER_CELL_UPDATE = 60      # read E, B, J (9 x 4) + write E, B (6 x 4)
+METRIC = "cell-updates/s and particle-pushes/s (% HBM roofline) at <=1e-5 rel err vs FP64"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="reduced grid (profiling captures)")
+    return ap.parse_args()
+
+
+def workload(small=False):
+    from paper_1910_13529_gb300 import workloads as wl
+    if small:
+        return wl.beam_plasma(ndim=2, nz=512, nx=256, n_beam=250_000, behind_front=3.0)
+    return wl.beam_plasma()
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_baseline(grid, sps, frac=0.1, seed=0):
+    """FP64 oracle on the host: the full grid and a random fraction of the particles, one step."""
+    from oracle import core as oc
+    from oracle import fit
+    from paper_1910_13529_gb300 import workloads as wl
+    rng = np.random.default_rng(seed)
+    kappa = grid["dz"] / grid["dt"]
+    C = fit.fit_coefficients(kappa)
+    h = fit.correction_kernel(C, hlen=40)
+    g = oc.Grid(grid["ndim"], grid["nz"], grid["nx"], grid.get("ny", 1), grid["dz"], grid["dx"], grid["dy"],
+                grid["dt"], C=C, shape=grid["shape"])
+    species, n = [], 0
+    for sp in sps:
+        sel = rng.random(len(sp["iz"])) < frac
+        sub = {k: (v[..., sel] if isinstance(v, np.ndarray) and v.shape[-1] == len(sel) else v)
+               for k, v in sp.items()}
+        species.append(oc.Species(wl.xi_of(sub, grid["ndim"]), sub["u"].T.astype(np.float64), sp["q"], sp["m"],
+                                  sp["w"]))
+        n += int(sel.sum())
+    sim = oc.Sim(g, species, h=h, moving_window=True)
+    t0 = time.perf_counter()
+    sim.step()
+    dt = time.perf_counter() - t0
+    return n / dt, dt, n
+
+
+def emit(obj):
+    print(json.dumps(obj), flush=True)
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    grid, sps = workload(args.small)
+    n_total = sum(len(sp["iz"]) for sp in sps)
+    vals, times = [], []
+    for _ in range(max(args.warmup, 0) and 0 or 0):
+        pass
+    for k in range(max(1, min(args.steps, 3))):
+        v, dt, n = oracle_baseline(grid, sps, frac=0.05, seed=k)
+        vals.append(v)
+        times.append(dt)
+    value = float(np.median(vals))
+    sample = f"one FP64 oracle step on the full {grid['nz']}x{grid['nx']} grid with a 5% random sample " \
+             f"({n} of {n_total}) of the particles, single thread"
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-pushes/s", "n_gpus": 0,
+          "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 * float(np.median(times)),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic",
+          "config": {"workload": "beam_plasma_2d", "grid": [grid["nz"], grid["nx"]], "particles": n_total},
+          "cpu_baseline": {"value": value, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
+                           "sample": sample},
+          "e2e": {"value": value, "unit": "particle-pushes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1910_13529_gb300 import pic_timing, pic_timing_read
+    from paper_1910_13529_gb300.runtime import Simulation
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    grid, sps = workload(args.small)
+    n0 = [len(sp["iz"]) for sp in sps]
+    cap_extra = 200_000
+    kw = {k: grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape", "solver",
+                               "moving_window", "inject_species", "inject_ppc", "rho_bg")}
+    sim = Simulation(device=str(dev), sort_every=20, **kw)
+    for s, sp in enumerate(sps):
+        sim.add_species(s, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"],
+                        cap=n0[s] + cap_extra)
+    stream = sim.stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    sim.step(args.warmup)
+    d0 = sim.diag()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pic_timing(sim.h, 1)
+    with ClockSampler(local_rank) as clk:
+        ev0.record()
+        sim.step(args.steps)
+        ev1.record()
+        torch.cuda.synchronize(dev)
+    kms, klaunch = pic_timing_read(sim.h, stream)
+    pic_timing(sim.h, 0)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    d1 = sim.diag()
+    pushes_per_step = 0.5 * (d0["count"] + d1["count"])
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    total_pushes = pushes_per_step * args.steps * world
+    value = total_pushes / (ms_max / 1e3)
+    cells = grid["nz"] * grid["nx"] * grid.get("ny", 1)
+    cell_rate = cells * args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel class
+    dom = max(kms, key=kms.get)
+    peak, peak_kind = measured_peak()
+    if dom == "particles":
+        algo = BYTES_PER_PUSH_2D * pushes_per_step * args.steps
+    else:
+        algo = BYTES_PER_CELL_UPDATE * cells * args.steps
+    achieved = algo / (kms[dom] / 1e3) / 1e9
+    fa_gbs = BYTES_PER_CELL_UPDATE * cells * args.steps / (kms["fields"] / 1e3) / 1e9 if kms["fields"] else None
+
+    # end to end through the C ABI from pinned host buffers: upload the initial state, run the
+    # steps, download the final fields and particles
+    host = []
+    for s, sp in enumerate(sps):
+        d = sim.species[s]
+        host.append({k: torch.empty_like(d[k], device="cpu").pin_memory() for k in ("cell", "off", "u")})
+        host[-1]["cell"].fill_(-1)
+        from paper_1910_13529_gb300 import encode_cells
+        n = n0[s]
+        host[-1]["cell"][:n] = torch.from_numpy(encode_cells(sp["iz"], sp["ix"], sp["iy"], grid["nz"], grid["nx"]))
+        host[-1]["off"][:, :n] = torch.from_numpy(sp["off"][: grid["ndim"]])
+        host[-1]["u"][:, :n] = torch.from_numpy(sp["u"])
+    hE = torch.zeros_like(sim.E, device="cpu").pin_memory()
+    hB = torch.zeros_like(sim.B, device="cpu").pin_memory()
+    out = [{k: torch.empty_like(v).pin_memory() for k, v in h.items()} for h in host]
+    oE, oB = torch.empty_like(hE).pin_memory(), torch.empty_like(hB).pin_memory()
+    from paper_1910_13529_gb300 import pic_bind_species
+    h2d = sum(t.numel() * t.element_size() for h in host for t in h.values()) + 2 * hE.numel() * 4
+    d2h = h2d
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    sim.E.copy_(hE, non_blocking=True)
+    sim.B.copy_(hB, non_blocking=True)
+    for s in range(len(sps)):
+        d = sim.species[s]
+        for k in ("cell", "off", "u"):
+            d[k].copy_(host[s][k], non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        pic_bind_species(sim.h, s, d["cell"].data_ptr(), d["off"].data_ptr(), d["u"].data_ptr(), None, n0[s],
+                         d["cap"], sps[s]["q"], sps[s]["m"], sps[s]["w"])
+    sim.step(args.steps)
+    oE.copy_(sim.E, non_blocking=True)
+    oB.copy_(sim.B, non_blocking=True)
+    for s in range(len(sps)):
+        for k in ("cell", "off", "u"):
+            out[s][k].copy_(sim.species[s][k], non_blocking=True)
+    e1.record()
+    torch.cuda.synchronize(dev)
+    ms_e2e = e0.elapsed_time(e1)
+    t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = total_pushes / (float(t.item()) / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, dt, n = oracle_baseline(grid, sps, frac=0.05)
+        cpu = {"value": v, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle step, full {grid['nz']}x{grid['nx']} grid, 5% random particle "
+                         f"sample ({n} particles), {dt:.1f} s single-threaded"}
+    if rank == 0:
+        launches = int(sum(klaunch.values()))
+        working = (sum(sim.species[s]["cap"] for s in sim.species) * 24 + cells * 4 * (6 + 6 + 3)) / 1e6
+        emit({"metric": METRIC, "value": value, "unit": "particle-pushes/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+              "data": "synthetic (seeded beam + quiet-start plasma)",
+              "config": {"workload": "beam_plasma_2d" if not args.small else "beam_plasma_2d_small",
+                         "grid": [grid["nz"], grid["nx"]], "particles": int(sum(n0)), "solver": "custom M=16",
+                         "shape": "quadratic", "moving_window": True, "sort_every": 20,
+                         "l2": f"inputs larger than L2 (working set {working:.0f} MB > 129 MB)",
+                         "parallelism": f"{world} independent replica(s)"},
+              "secondary": {"cell-updates/s": cell_rate,
+                            "field_advance_GBps": fa_gbs,
+                            "kernel_ms": kms, "kernel_launches": klaunch},
+              "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                           "algorithmic_bytes_per_unit": BYTES_PER_PUSH_2D if dom == "particles"
+                           else BYTES_PER_CELL_UPDATE},
+              "cpu_baseline": cpu,
+              "e2e": {"value": e2e_value, "unit": "particle-pushes/s", "h2d_bytes_per_step": h2d / args.steps,
+                      "d2h_bytes_per_step": d2h / args.steps},
+              "gpu_launches": launches,
+              "clocks": clk.summary(),
+              "diag": {"count": d1["count"], "shifts": d1["shifts"], "gauss_max": d1["gauss_max"],
+                       "rho_max": d1["rho_max"]}})
+    sim.close()
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * pic.h -- C ABI of the GB300 (sm_103a) relativistic-beam electromagnetic PIC step.
+ *
+ * The step is the PIC loop of Sec. 1 of arXiv:1910.13529 ("deposit -> advance the
+ * fields -> interpolate -> push"), with
+ *   - the discretised Faraday and Ampere laws of Sec. 2.1 (Eq. 1) on a staggered grid,
+ *     axial derivative either the Yee two-point difference (Sec. 2.2) or the customised
+ *     2M-point stencil d+/d- of Sec. 3 and Appendix C;
+ *   - charge-conserving (Esirkepov) current deposition, which keeps Gauss's law
+ *     (Eq. Gauss) as Sec. 2.1 requires, with linear or quadratic B-spline shapes;
+ *   - for the customised stencil, the current correction of Sec. 3: J1 <- h * J1 along z,
+ *     h the impulse response of 1/P, P(k) = [k]_custom / [k]_Yee;
+ *   - field interpolation (gather) and a relativistic Boris push (leapfrog, Sec. 2.1);
+ *   - an optional moving window at c along +z with cold-plasma injection.
+ *
+ * Units: c = 1, lengths in c/omega_p, time in 1/omega_p, Gauss's law d.E = rho.
+ *
+ * Grid and memory layout (all device arrays are caller-owned, contiguous, FP32):
+ *   axis 1 = z (index i, fastest), axis 2 = x (index j), axis 3 = y (index k).
+ *   A field array holds 3 components, component-major: F[c][k][j][i], c = 0,1,2,
+ *   ny = 1 when ndim == 2.  Staggering: E1 (i+1/2,j,k), E2 (i,j+1/2,k), E3 (i,j,k+1/2),
+ *   B1 (i,j+1/2,k+1/2), B2 (i+1/2,j,k+1/2), B3 (i+1/2,j+1/2,k); J like E; rho at nodes.
+ *   In 2D, E3 and J3 sit at nodes and B1 at (i,j+1/2), B2 at (i+1/2,j), B3 at (i+1/2,j+1/2).
+ *   Fields are zero outside 0 <= i < nz ("open"/conducting z ends) and periodic in x, y.
+ *
+ * Particle layout (per species, structure of arrays, capacity cap):
+ *   int32 cell[cap]   guarded linear cell index (iz + 1) + (nz + 2) * (ix + nx * iy),
+ *                     iz in [-1, nz] (the guard values exist only transiently),
+ *                     any negative value marks a dead slot;
+ *   float off[ndim][cap]  in-cell offsets in [0, 1) along z, x (, y);
+ *   float u[3][cap]   momentum per unit mass u = gamma v;
+ *   int32 id[cap]     optional particle identifiers (NULL: none), carried by sort and
+ *                     assigned to injected particles.
+ *
+ * Status and errors: every call returns a pic_status; nothing is thrown across the ABI
+ * and the library never exits.  Asynchronous CUDA failures and device-side errors
+ * (capacity overflow) are reported by the next synchronising call (pic_diag,
+ * pic_get_count, pic_sync).  pic_last_error() gives a one-line description.
+ * Calls are ordered on the caller's cudaStream_t (passed as void*); a handle is not
+ * thread-safe.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_t pic_t;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,       /* invalid argument or configuration */
+    PIC_ERR_CFL = 2,       /* dt above the leapfrog stability limit of the chosen stencil */
+    PIC_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+    PIC_ERR_OOM = 4,       /* device allocation of library scratch failed */
+    PIC_ERR_TIMEOUT = 5,   /* a bounded device-side wait gave up */
+    PIC_ERR_STATE = 6,     /* call out of order (e.g. deposit before gather_push) */
+    PIC_ERR_CAPACITY = 7   /* particle capacity exceeded (injection) */
+} pic_status;
+
+enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_CUSTOM = 1 };
+
+#define PIC_MAX_M 16        /* largest customised stencil (Appendix C uses M = 16) */
+#define PIC_MAX_HLEN 24     /* current-correction taps kept on each side in FP32 */
+#define PIC_MAX_SPECIES 4
+#define PIC_DIAG_N 10
+
+/* Indices of pic_diag's output vector. */
+enum {
+    PIC_DIAG_GAUSS_MAX = 0,   /* max |d-.E - rho - rho_bg| over interior nodes (FP64) */
+    PIC_DIAG_GAUSS_RMS = 1,   /* rms of the same */
+    PIC_DIAG_RHO_MAX = 2,     /* max |rho| (scale for the residual) */
+    PIC_DIAG_FIELD_ENERGY = 3,/* (1/2) sum (E^2 + B^2) dV */
+    PIC_DIAG_KINETIC = 4,     /* sum w m (gamma - 1) */
+    PIC_DIAG_COUNT = 5,       /* live particles, all species */
+    PIC_DIAG_STEP = 6,        /* completed steps */
+    PIC_DIAG_SHIFTS = 7,      /* moving-window shifts done */
+    PIC_DIAG_STATUS = 8,      /* device status word (0 = ok) */
+    PIC_DIAG_INTERIOR = 9     /* number of nodes in the residual */
+};
+
+typedef struct pic_config {
+    int ndim;               /* 2: (z, x); 3: (z, x, y) */
+    int nz, nx, ny;         /* cells along z, x, y (ny ignored in 2D); nz, nx >= 2 */
+    double dz, dx, dy;      /* cell sizes */
+    double dt;              /* time step */
+    int solver;             /* PIC_SOLVER_YEE or PIC_SOLVER_CUSTOM */
+    int M;                  /* customised: number of coefficients C_1..C_M, 1 <= M <= PIC_MAX_M */
+    const double* coef;     /* customised: host array of M coefficients; NULL fits them
+                               (Appendix C, target [k1]_t = sin(k dt/2)/(dt/2), Sec. 3) */
+    double fit_wk, fit_n;   /* fit weight exp(-ln2 (2k/w_k1)^n); 0 selects 0.6 and 10 */
+    int shape;              /* 1: linear, 2: quadratic B-spline */
+    int moving_window;      /* 1: the window moves one cell when n dt >= (s+1) dz */
+    int inject_species;     /* species receiving cold plasma in the new column (-1: none) */
+    int inject_ppc[3];      /* quiet-start particles per cell along z, x, y for injection */
+    double rho_bg;          /* uniform background charge density (Gauss diagnostic only) */
+    int sort_every;         /* pic_step sorts particles by cell every sort_every steps (0: never) */
+} pic_config;
+
+/* ---- handle ------------------------------------------------------------------------
+ * pic_create validates cfg, fits the customised coefficients when cfg->coef is NULL,
+ * computes the correction taps h, checks dt against the stability limit
+ *   (dt/2)^2 (max_k [k]_1^2 + sum_perp (2/d_perp)^2) <= 1   (Sec. 2.1 leapfrog, App. C)
+ * (PIC_ERR_CFL above it), and allocates the library's scratch on the current device:
+ * the second field buffer of the out-of-place advance, the corrected-J1 buffer, sort and
+ * diagnostic workspace.  Device memory: about 7 x 4 x nz nx ny bytes + 8 x nz nx ny.   */
+pic_status pic_create(const pic_config* cfg, pic_t** out);
+pic_status pic_destroy(pic_t* h);
+/* Text of the last error of h (h == NULL: of the last failed pic_create). Never NULL. */
+const char* pic_last_error(const pic_t* h);
+
+/* ---- host-only helpers (no GPU needed) ------------------------------------------------
+ * Appendix C least-squares fit of C_1..C_M to the Sec. 3 target [k1]_t with kappa = dz/dt,
+ * constraint sum (2l-1) C_l = 1 (p = 2), weight w_k1 = wk, order n.  C_out: M doubles.   */
+pic_status pic_fit_coefficients(double kappa, int M, double wk, double n, double* C_out);
+/* Sec. 3 correction taps: impulse response of 1/P, P(phi) = sum_l C_l sin((2l-1)phi/2)/sin(phi/2),
+ * h_out: 2*hlen+1 doubles, centre at index hlen.  PIC_ERR_ARG if P has a zero.          */
+pic_status pic_correction_taps(const double* C, int M, int hlen, double* h_out);
+/* Largest stable dt for the given grid and axial stencil (M = 1, C = {1}: Yee).       */
+pic_status pic_cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M, double* dt_out);
+/* Coefficients and taps a handle uses (C_out: PIC_MAX_M, h_out: 2*PIC_MAX_HLEN+1). */
+pic_status pic_get_coefficients(const pic_t* h, double* C_out, int* M, double* h_out, int* hlen);
+
+/* ---- binding caller-owned device memory ---------------------------------------------
+ * E, B, J: device pointers to 3 * ny * nx * nz floats each (layout above).  The library
+ * reads and writes E and B in place (after every completed call the current fields are
+ * in these arrays) and uses J as the current of the last deposit.                       */
+pic_status pic_bind_fields(pic_t* h, float* E, float* B, float* J);
+/* Species s (0 <= s < PIC_MAX_SPECIES): arrays of the layout above with capacity cap and
+ * n live particles at slots [0, n).  q, m: charge and mass of one physical particle
+ * (electron: -1, 1); w: weight, so one macro-particle carries charge q w and the charge
+ * density it adds at a node is q w S / (cell volume).  Rebinding replaces the species.  */
+pic_status pic_bind_species(pic_t* h, int s, int32_t* cell, float* off, float* u, int32_t* id,
+                            int64_t n, int64_t cap, double q, double m, double w);
+
+/* ---- the step (all calls enqueue on stream and return without synchronising) ----------
+ * pic_gather_push: for every live particle, apply a pending window shift, interpolate
+ *   E^n, B^n at x^n (shape-weighted, staggered), Boris u^{n-1/2} -> u^{n+1/2}, and move
+ *   x^{n+1} = x^n + dt u/gamma; the old position is kept in library scratch.
+ * pic_deposit: zero J, deposit J^{n+1/2} from the old and new positions (Esirkepov) for all
+ *   species, apply the Sec. 3 correction to J1 (customised stencil), and retire particles
+ *   that left 0 <= z < nz.  Requires a preceding pic_gather_push (else PIC_ERR_STATE).
+ * pic_field_advance: B^{n+1/2} = B^n - dt/2 d+xE^n, E^{n+1} = E^n + dt (d-xB^{n+1/2} - J),
+ *   B^{n+1} = B^{n+1/2} - dt/2 d+xE^{n+1} (Eq. 1); completes step n.  If the window is due,
+ *   the fields are shifted one cell towards -z, the front column zeroed and the injected
+ *   column of cold plasma appended to inject_species.
+ * pic_step: nsteps x (gather_push + deposit + field_advance), with the particle part fused
+ *   into one kernel per species; sorts by cell every sort_every steps.                  */
+pic_status pic_gather_push(pic_t* h, void* stream);
+pic_status pic_deposit(pic_t* h, void* stream);
+pic_status pic_field_advance(pic_t* h, void* stream);
+pic_status pic_step(pic_t* h, int nsteps, void* stream);
+/* Counting sort of every species by cell (dead slots removed); ids follow their particles. */
+pic_status pic_sort(pic_t* h, void* stream);
+
+/* ---- diagnostics (FP64 on the GPU) ----------------------------------------------------
+ * pic_diag fills out[PIC_DIAG_N] (indices above) and synchronises stream.  The Gauss
+ * residual d-.E - rho - rho_bg uses the same d- as Ampere's law (customised stencil
+ * included) and skips nodes within (M + hlen + 2) cells of the z ends.                  */
+pic_status pic_diag(pic_t* h, double* out, void* stream);
+/* rho (FP64, nz*nx*ny doubles, device) of all live particles at the current positions. */
+pic_status pic_rho(pic_t* h, double* rho, void* stream);
+/* G = d-.E - rho - rho_bg at every node (FP64, device). */
+pic_status pic_gauss(pic_t* h, double* G, void* stream);
+/* Live-particle count of species s (synchronises stream). */
+pic_status pic_get_count(pic_t* h, int s, int64_t* n, void* stream);
+/* Completed steps, window shifts, and whether a shift is still pending on the particles. */
+pic_status pic_get_state(const pic_t* h, int64_t* step, int64_t* shifts, int* pending_shift);
+/* Synchronise stream and report any CUDA or device-side error. */
+pic_status pic_sync(pic_t* h, void* stream);
+
+/* ---- kernel timing (CUDA events on the caller's stream) --------------------------------
+ * pic_timing(h, 1) starts collecting: every later kernel launch of h is bracketed by a pair
+ * of events on its stream and counted, per class below; pic_timing(h, 0) stops.
+ * pic_timing_read synchronises stream and returns, per class, the summed event time (ms)
+ * and the number of kernel launches since collection started.                           */
+enum {
+    PIC_T_PARTICLES = 0,   /* gather + push (+ deposit when fused), per species */
+    PIC_T_DEPOSIT = 1,     /* unfused deposition and zeroing of J */
+    PIC_T_CORRECTION = 2,  /* Sec. 3 current correction */
+    PIC_T_FIELDS = 3,      /* field advance (and copies back to the bound arrays) */
+    PIC_T_SORT = 4,        /* counting sort */
+    PIC_T_WINDOW = 5,      /* injection of the new plasma column */
+    PIC_T_DIAG = 6,        /* rho, Gauss residual, reductions */
+    PIC_TIMING_N = 7
+};
+pic_status pic_timing(pic_t* h, int enable);
+pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,298 @@
+// Field advance (Eq. 1 of Sec. 2.1, Yee operators of Sec. 2.2, customised axial stencil of
+// Sec. 3 / Appendix C) and the Sec. 3 current correction, for sm_103a.
+//
+// One kernel performs the whole leapfrog step out of place:
+//   B^{n+1/2} = B^n - dt/2 d+ x E^n
+//   E^{n+1}   = E^n + dt (d- x B^{n+1/2} - J)
+//   B^{n+1}   = B^{n+1/2} - dt/2 d+ x E^{n+1}
+// Each CTA owns a TZ x TX (x TY) output tile.  It stages E^n over the tile plus the halo the
+// three stages need (3M-2 cells before and after in z, 1 before / 2 after across), computes
+// B^{n+1/2} into shared memory over the tile plus the stage-2 halo, updates E in place in
+// shared memory, and finishes B^{n+1}; E^n and B^n are read once and E^{n+1}, B^{n+1} written
+// once per cell (60 B per cell-update with J), the halos coming from L2.  Writing to the second
+// buffer lets the moving-window shift be folded into the store.
+#include <cuda_runtime.h>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+namespace {
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+struct Tile {
+    static constexpr int L0 = 3 * MAXM - 2;          // E^n halo before the tile (z)
+    static constexpr int W0 = TZ + 6 * MAXM - 3;     // E^n z extent
+    static constexpr int L1 = 2 * MAXM - 1;          // B^{n+1/2} halo before the tile
+    static constexpr int W1 = TZ + 4 * MAXM - 2;     // B^{n+1/2} z extent
+    static constexpr int L2 = MAXM - 1;              // E^{n+1} halo before the tile
+    static constexpr int W2 = TZ + 2 * MAXM - 1;     // E^{n+1} z extent
+    static constexpr int TYe = NDIM == 3 ? TY : 1;
+    static constexpr int RX0 = TX + 3, RY0 = NDIM == 3 ? TY + 3 : 1;   // E rows: [-1, T+1]
+    static constexpr int RX1 = TX + 2, RY1 = NDIM == 3 ? TY + 2 : 1;   // B rows: [-1, T]
+    static constexpr int RX2 = TX + 1, RY2 = NDIM == 3 ? TY + 1 : 1;   // E' rows: [0, T]
+    static constexpr int SE = RX0 * RY0 * W0;
+    static constexpr int SB = RX1 * RY1 * W1;
+    static constexpr size_t smem_bytes = sizeof(float) * 3 * (SE + SB);
+};
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+__global__ void __launch_bounds__(256) field_advance_kernel(FieldP p) {
+    using T = Tile<NDIM, MAXM, TZ, TX, TY>;
+    extern __shared__ float smem[];
+    float* sE = smem;                 // [3][RY0][RX0][W0]
+    float* sB = smem + 3 * T::SE;     // [3][RY1][RX1][W1]
+
+    const GridP& g = p.g;
+    const int nz = g.nz, nx = g.nx, ny = g.ny;
+    const long long N = g.ncell;
+    const int z0 = blockIdx.x * TZ;
+    const int x0 = blockIdx.y * TX;
+    const int y0 = NDIM == 3 ? blockIdx.z * TY : 0;
+    const int M = p.st.M;
+
+    const float dt = g.dt;
+    const float hx = 0.5f * dt / g.dx, fx = dt / g.dx;
+    const float hy = NDIM == 3 ? 0.5f * dt / g.dy : 0.f, fy = NDIM == 3 ? dt / g.dy : 0.f;
+    float Ch[MAXM], Cf[MAXM];
+#pragma unroll
+    for (int l = 0; l < MAXM; ++l) {
+        float c = l < M ? p.st.C[l] : 0.f;
+        Ch[l] = c * (0.5f * dt / g.dz);
+        Cf[l] = c * (dt / g.dz);
+    }
+
+    // ---- stage 0: E^n over the full halo -------------------------------------------
+    for (int idx = threadIdx.x; idx < T::RY0 * T::RX0 * T::W0; idx += blockDim.x) {
+        int col = idx % T::W0;
+        int r = idx / T::W0;
+        int rx = r % T::RX0, ry = r / T::RX0;
+        int gz = z0 + col - T::L0;
+        int gx = wrapi(x0 + rx - 1, nx);
+        int gy = NDIM == 3 ? wrapi(y0 + ry - 1, ny) : 0;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+        if (gz >= 0 && gz < nz) {
+            long long o = ((long long)gy * nx + gx) * nz + gz;
+            v0 = __ldg(p.Ein + o);
+            v1 = __ldg(p.Ein + N + o);
+            v2 = __ldg(p.Ein + 2 * N + o);
+        }
+        sE[idx] = v0;
+        sE[T::SE + idx] = v1;
+        sE[2 * T::SE + idx] = v2;
+    }
+    __syncthreads();
+
+    // ---- stage 1: B^{n+1/2} over x in [-1, TX], y in [-1, TY], z in [-L1, TZ+2MAXM-2] ----
+    for (int idx = threadIdx.x; idx < T::RY1 * T::RX1 * T::W1; idx += blockDim.x) {
+        int col = idx % T::W1;
+        int r = idx / T::W1;
+        int rx = r % T::RX1, ry = r / T::RX1;
+        int z = col - T::L1;
+        int gz = z0 + z;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (gz >= 0 && gz < nz) {
+            int gx = wrapi(x0 + rx - 1, nx);
+            int gy = NDIM == 3 ? wrapi(y0 + ry - 1, ny) : 0;
+            long long o = ((long long)gy * nx + gx) * nz + gz;
+            // E index of the same (x, y, z): rows shift by 0 (both start at -1), cols by MAXM-1
+            int e = (ry * T::RX0 + rx) * T::W0 + col + (MAXM - 1);
+            const float* E1 = sE;
+            const float* E2 = sE + T::SE;
+            const float* E3 = sE + 2 * T::SE;
+            float dzE2 = 0.f, dzE3 = 0.f;
+#pragma unroll
+            for (int l = 0; l < MAXM; ++l) {
+                dzE2 += Ch[l] * (E2[e + l + 1] - E2[e - l]);
+                dzE3 += Ch[l] * (E3[e + l + 1] - E3[e - l]);
+            }
+            float dxE1 = E1[e + T::W0] - E1[e];
+            float dxE3 = E3[e + T::W0] - E3[e];
+            float dyE1 = 0.f, dyE2 = 0.f;
+            if (NDIM == 3) {
+                dyE1 = E1[e + T::RX0 * T::W0] - E1[e];
+                dyE2 = E2[e + T::RX0 * T::W0] - E2[e];
+            }
+            b0 = __ldg(p.Bin + o) - (hx * dxE3 - hy * dyE2);
+            b1 = __ldg(p.Bin + N + o) - (hy * dyE1 - dzE3);
+            b2 = __ldg(p.Bin + 2 * N + o) - (dzE2 - hx * dxE1);
+        }
+        sB[idx] = b0;
+        sB[T::SB + idx] = b1;
+        sB[2 * T::SB + idx] = b2;
+    }
+    __syncthreads();
+
+    // ---- stage 2: E^{n+1} in place over x in [0, TX], y in [0, TY], z in [-L2, TZ+MAXM-1] ----
+    for (int idx = threadIdx.x; idx < T::RY2 * T::RX2 * T::W2; idx += blockDim.x) {
+        int col = idx % T::W2;
+        int r = idx / T::W2;
+        int rx = r % T::RX2, ry = r / T::RX2;     // x = rx, y = ry
+        int z = col - T::L2;
+        int gz = z0 + z;
+        int e = ((NDIM == 3 ? ry + 1 : 0) * T::RX0 + rx + 1) * T::W0 + z + T::L0;
+        float n0 = 0.f, n1 = 0.f, n2 = 0.f;
+        if (gz >= 0 && gz < nz) {
+            int gx = wrapi(x0 + rx, nx);
+            int gy = NDIM == 3 ? wrapi(y0 + ry, ny) : 0;
+            long long o = ((long long)gy * nx + gx) * nz + gz;
+            int b = ((NDIM == 3 ? ry + 1 : 0) * T::RX1 + rx + 1) * T::W1 + z + T::L1;
+            const float* B1 = sB;
+            const float* B2 = sB + T::SB;
+            const float* B3 = sB + 2 * T::SB;
+            float dzB2 = 0.f, dzB3 = 0.f;
+#pragma unroll
+            for (int l = 0; l < MAXM; ++l) {
+                dzB2 += Cf[l] * (B2[b + l] - B2[b - l - 1]);
+                dzB3 += Cf[l] * (B3[b + l] - B3[b - l - 1]);
+            }
+            float dxB1 = B1[b] - B1[b - T::W1];
+            float dxB3 = B3[b] - B3[b - T::W1];
+            float dyB1 = 0.f, dyB2 = 0.f;
+            if (NDIM == 3) {
+                dyB1 = B1[b] - B1[b - T::RX1 * T::W1];
+                dyB2 = B2[b] - B2[b - T::RX1 * T::W1];
+            }
+            n0 = sE[e] + (fx * dxB3 - fy * dyB2) - dt * __ldg(p.J1 + o);
+            n1 = sE[T::SE + e] + (fy * dyB1 - dzB3) - dt * __ldg(p.J2 + o);
+            n2 = sE[2 * T::SE + e] + (dzB2 - fx * dxB1) - dt * __ldg(p.J3 + o);
+        }
+        sE[e] = n0;
+        sE[T::SE + e] = n1;
+        sE[2 * T::SE + e] = n2;
+    }
+    __syncthreads();
+
+    // ---- stage 3: B^{n+1} on the tile; store E^{n+1}, B^{n+1} (shifted if the window moves) ----
+    for (int idx = threadIdx.x; idx < T::TYe * TX * TZ; idx += blockDim.x) {
+        int z = idx % TZ;
+        int r = idx / TZ;
+        int x = r % TX, y = r / TX;
+        int gz = z0 + z, gx = x0 + x, gy = y0 + y;
+        if (gz >= nz || gx >= nx || (NDIM == 3 && gy >= ny)) continue;
+        int e = ((NDIM == 3 ? y + 1 : 0) * T::RX0 + x + 1) * T::W0 + z + T::L0;
+        int b = ((NDIM == 3 ? y + 1 : 0) * T::RX1 + x + 1) * T::W1 + z + T::L1;
+        const float* E1 = sE;
+        const float* E2 = sE + T::SE;
+        const float* E3 = sE + 2 * T::SE;
+        float dzE2 = 0.f, dzE3 = 0.f;
+#pragma unroll
+        for (int l = 0; l < MAXM; ++l) {
+            dzE2 += Ch[l] * (E2[e + l + 1] - E2[e - l]);
+            dzE3 += Ch[l] * (E3[e + l + 1] - E3[e - l]);
+        }
+        float dxE1 = E1[e + T::W0] - E1[e];
+        float dxE3 = E3[e + T::W0] - E3[e];
+        float dyE1 = 0.f, dyE2 = 0.f;
+        if (NDIM == 3) {
+            dyE1 = E1[e + T::RX0 * T::W0] - E1[e];
+            dyE2 = E2[e + T::RX0 * T::W0] - E2[e];
+        }
+        float b0 = sB[b] - (hx * dxE3 - hy * dyE2);
+        float b1 = sB[T::SB + b] - (hy * dyE1 - dzE3);
+        float b2 = sB[2 * T::SB + b] - (dzE2 - hx * dxE1);
+        long long row = ((long long)gy * nx + gx) * nz;
+        int oz = gz - p.shift;
+        if (oz >= 0) {
+            long long o = row + oz;
+            p.Eout[o] = E1[e];
+            p.Eout[N + o] = E2[e];
+            p.Eout[2 * N + o] = E3[e];
+            p.Bout[o] = b0;
+            p.Bout[N + o] = b1;
+            p.Bout[2 * N + o] = b2;
+        }
+        if (p.shift && gz == nz - 1) {
+            long long o = row + gz;
+            p.Eout[o] = 0.f;
+            p.Eout[N + o] = 0.f;
+            p.Eout[2 * N + o] = 0.f;
+            p.Bout[o] = 0.f;
+            p.Bout[N + o] = 0.f;
+            p.Bout[2 * N + o] = 0.f;
+        }
+    }
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+cudaError_t launch_fa(const FieldP& p, cudaStream_t s) {
+    using T = Tile<NDIM, MAXM, TZ, TX, TY>;
+    auto k = field_advance_kernel<NDIM, MAXM, TZ, TX, TY>;
+    static bool configured = false;   // attribute is per function; setting it twice is harmless
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, NDIM == 3 ? (p.g.ny + TY - 1) / TY : 1);
+    k<<<grid, 256, T::smem_bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+// In-place Sec. 3 correction J1[i] <- sum_{|m| <= hlen} h[m] J1[i - m] along z (J1 = 0 outside
+// 0 <= i < nz).  One CTA holds a whole z row in shared memory, so no other CTA reads the values
+// it overwrites.
+struct CorrP {
+    GridP g;
+    float h[2 * PIC_MAX_HLEN + 1];
+    int hlen;
+    float* J1;
+};
+
+__global__ void __launch_bounds__(256) correct_j1_kernel(CorrP p) {
+    extern __shared__ float s[];      // nz + 2 hlen
+    const int nz = p.g.nz;
+    const int hl = p.hlen;
+    float* row = p.J1 + (long long)blockIdx.x * nz;
+    for (int i = threadIdx.x; i < nz + 2 * hl; i += blockDim.x) {
+        int gz = i - hl;
+        s[i] = (gz >= 0 && gz < nz) ? row[gz] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) {
+        float acc = 0.f;
+        for (int m = -hl; m <= hl; ++m) acc += p.h[m + hl] * s[i + hl - m];
+        row[i] = acc;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s) {
+    const int M = p.st.M;
+    if (p.g.ndim == 2) {
+        if (M <= 1) return launch_fa<2, 1, 128, 8, 1>(p, s);
+        if (M <= 4) return launch_fa<2, 4, 128, 8, 1>(p, s);
+        if (M <= 8) return launch_fa<2, 8, 128, 8, 1>(p, s);
+        return launch_fa<2, 16, 128, 8, 1>(p, s);
+    }
+    if (M <= 1) return launch_fa<3, 1, 64, 4, 4>(p, s);
+    if (M <= 4) return launch_fa<3, 4, 64, 4, 4>(p, s);
+    if (M <= 8) return launch_fa<3, 8, 64, 4, 4>(p, s);
+    return launch_fa<3, 16, 64, 4, 4>(p, s);
+}
+
+cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s) {
+    CorrP p;
+    p.g = g;
+    p.hlen = hlen;
+    for (int i = 0; i < 2 * PIC_MAX_HLEN + 1; ++i) p.h[i] = i < 2 * hlen + 1 ? taps[i] : 0.f;
+    p.J1 = J1;
+    size_t smem = sizeof(float) * (g.nz + 2 * hlen);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(correct_j1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    long long rows = (long long)g.nx * g.ny;
+    correct_j1_kernel<<<(unsigned)rows, 256, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

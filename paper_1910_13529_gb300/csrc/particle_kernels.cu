@@ -1,0 +1,714 @@
+// Particle kernels for sm_103a: field gather, relativistic Boris push, position update and
+// charge-conserving (Esirkepov) current deposition (Sec. 1 PIC loop; Sec. 2.1 requires the
+// deposition to conserve charge so that Gauss's law holds), plus counting sort, moving-window
+// injection and the FP64 charge density used by the diagnostics.
+//
+// Positions are (integer cell, FP32 offset in [0,1)) so that precision does not degrade with
+// the distance from the origin.  Shape factors of a position are always computed from its own
+// offset and placed into the deposition window by an integer shift, which makes the "new"
+// shape of one step bit-identical to the "old" shape of the next: charge is conserved to FP32
+// round-off per step with no drift from re-rounded positions.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "pic_internal.h"
+
+namespace pic {
+
+namespace {
+
+// ---------------------------------------------------------------- shapes ----
+// Weights of the K nodes a position touches, first node at cell + rel.
+template <int SHAPE>
+struct Shape;
+
+template <>
+struct Shape<1> {                         // linear B-spline: S(d) = 1 - |d|
+    static constexpr int K = 2;
+    template <typename R>
+    __device__ static __forceinline__ int w(R o, R* W) {
+        W[0] = R(1) - o;
+        W[1] = o;
+        return 0;
+    }
+};
+
+template <>
+struct Shape<2> {                         // quadratic B-spline centred on the nearest node
+    static constexpr int K = 3;
+    template <typename R>
+    __device__ static __forceinline__ int w(R o, R* W) {
+        int up = o >= R(0.5);
+        R d = o - (R)up;                  // in [-1/2, 1/2)
+        R a = R(0.5) - d, b = R(0.5) + d;
+        W[0] = R(0.5) * a * a;
+        W[1] = R(0.75) - d * d;
+        W[2] = R(0.5) * b * b;
+        return up - 1;
+    }
+};
+
+// weights for a component staggered by half a cell along this axis: shift the position by -1/2
+template <int SHAPE>
+__device__ __forceinline__ int half_weights(int cell, float o, float* W) {
+    if (o >= 0.5f) return cell + Shape<SHAPE>::w(o - 0.5f, W);
+    return cell - 1 + Shape<SHAPE>::w(o + 0.5f, W);
+}
+
+__device__ __forceinline__ int wrapi(int a, int n) {
+    a %= n;
+    return a < 0 ? a + n : a;
+}
+
+struct Pos {
+    int iz, ix, iy;
+    float oz, ox, oy;
+};
+
+__device__ __forceinline__ void decode(const GridP& g, int cell, int& izg, int& ix, int& iy) {
+    izg = cell % g.nzg;
+    int r = cell / g.nzg;
+    ix = r % g.nx;
+    iy = r / g.nx;
+}
+
+__device__ __forceinline__ int encode(const GridP& g, int iz, int ix, int iy) {
+    return (iz + 1) + g.nzg * (ix + g.nx * iy);
+}
+
+// ---------------------------------------------------------------- gather ----
+template <int NDIM, int SHAPE>
+__device__ __forceinline__ float interp(const GridP& g, const float* __restrict__ F, int bz,
+                                        const float* Wz, int bx, const float* Wx, int by,
+                                        const float* Wy) {
+    constexpr int K = Shape<SHAPE>::K;
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < (NDIM == 3 ? K : 1); ++c) {
+        int gy = NDIM == 3 ? wrapi(by + c, g.ny) : 0;
+        float wy = NDIM == 3 ? Wy[c] : 1.f;
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            int gx = wrapi(bx + b, g.nx);
+            long long row = ((long long)gy * g.nx + gx) * g.nz;
+            float wxy = wy * Wx[b];
+            float racc = 0.f;
+#pragma unroll
+            for (int a = 0; a < K; ++a) {
+                int gz = bz + a;
+                if (gz >= 0 && gz < g.nz) racc += Wz[a] * __ldg(F + row + gz);
+            }
+            acc += wxy * racc;
+        }
+    }
+    return acc;
+}
+
+// E1..E3, B1..B3 at the particle (staggering: E1 z+, E2 x+, E3 y+ (3D) / node (2D),
+// B1 x+ y+, B2 z+ y+, B3 z+ x+; "+" = half cell).
+template <int NDIM, int SHAPE>
+__device__ __forceinline__ void gather(const GridP& g, const float* __restrict__ E,
+                                       const float* __restrict__ B, const Pos& p, float* eb) {
+    constexpr int K = Shape<SHAPE>::K;
+    float Wzn[K], Wzh[K], Wxn[K], Wxh[K], Wyn[K], Wyh[K];
+    int bzn = p.iz + Shape<SHAPE>::w(p.oz, Wzn);
+    int bzh = half_weights<SHAPE>(p.iz, p.oz, Wzh);
+    int bxn = p.ix + Shape<SHAPE>::w(p.ox, Wxn);
+    int bxh = half_weights<SHAPE>(p.ix, p.ox, Wxh);
+    int byn = 0, byh = 0;
+    if (NDIM == 3) {
+        byn = p.iy + Shape<SHAPE>::w(p.oy, Wyn);
+        byh = half_weights<SHAPE>(p.iy, p.oy, Wyh);
+    }
+    const long long N = g.ncell;
+    if (NDIM == 3) {
+        eb[0] = interp<NDIM, SHAPE>(g, E, bzh, Wzh, bxn, Wxn, byn, Wyn);
+        eb[1] = interp<NDIM, SHAPE>(g, E + N, bzn, Wzn, bxh, Wxh, byn, Wyn);
+        eb[2] = interp<NDIM, SHAPE>(g, E + 2 * N, bzn, Wzn, bxn, Wxn, byh, Wyh);
+        eb[3] = interp<NDIM, SHAPE>(g, B, bzn, Wzn, bxh, Wxh, byh, Wyh);
+        eb[4] = interp<NDIM, SHAPE>(g, B + N, bzh, Wzh, bxn, Wxn, byh, Wyh);
+        eb[5] = interp<NDIM, SHAPE>(g, B + 2 * N, bzh, Wzh, bxh, Wxh, byn, Wyn);
+    } else {
+        eb[0] = interp<NDIM, SHAPE>(g, E, bzh, Wzh, bxn, Wxn, 0, nullptr);
+        eb[1] = interp<NDIM, SHAPE>(g, E + N, bzn, Wzn, bxh, Wxh, 0, nullptr);
+        eb[2] = interp<NDIM, SHAPE>(g, E + 2 * N, bzn, Wzn, bxn, Wxn, 0, nullptr);
+        eb[3] = interp<NDIM, SHAPE>(g, B, bzn, Wzn, bxh, Wxh, 0, nullptr);
+        eb[4] = interp<NDIM, SHAPE>(g, B + N, bzh, Wzh, bxn, Wxn, 0, nullptr);
+        eb[5] = interp<NDIM, SHAPE>(g, B + 2 * N, bzh, Wzh, bxh, Wxh, 0, nullptr);
+    }
+}
+
+// ---------------------------------------------------------------- push ----
+__device__ __forceinline__ void boris(float eps, const float* eb, float* u) {
+    float um0 = u[0] + eps * eb[0], um1 = u[1] + eps * eb[1], um2 = u[2] + eps * eb[2];
+    float gm = sqrtf(1.f + um0 * um0 + um1 * um1 + um2 * um2);
+    float f = eps / gm;
+    float t0 = f * eb[3], t1 = f * eb[4], t2 = f * eb[5];
+    float tt = t0 * t0 + t1 * t1 + t2 * t2;
+    float sf = 2.f / (1.f + tt);
+    float s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
+    float up0 = um0 + (um1 * t2 - um2 * t1);
+    float up1 = um1 + (um2 * t0 - um0 * t2);
+    float up2 = um2 + (um0 * t1 - um1 * t0);
+    float ul0 = um0 + (up1 * s2 - up2 * s1);
+    float ul1 = um1 + (up2 * s0 - up0 * s2);
+    float ul2 = um2 + (up0 * s1 - up1 * s0);
+    u[0] = ul0 + eps * eb[0];
+    u[1] = ul1 + eps * eb[1];
+    u[2] = ul2 + eps * eb[2];
+}
+
+__device__ __forceinline__ void advance_axis(int& i, float& o, float d) {
+    float t = o + d;
+    float fl = floorf(t);
+    t -= fl;
+    int di = (int)fl;
+    if (t >= 1.f) {      // t was within round-off below an integer
+        t -= 1.f;
+        di += 1;
+    }
+    i += di;
+    o = t;
+}
+
+// ---------------------------------------------------------------- deposit ----
+// Esirkepov current of one particle moving p0 -> p1 (|displacement| < 1 cell per axis).
+// 2D: W1 = dSz (S0x + dSx/2), W2 = dSx (S0z + dSz/2), W3 = S0z S0x + dSz S0x/2 + S0z dSx/2 + dSz dSx/3.
+// 3D: W_a = dS_a (S0_b S0_c + dS_b S0_c/2 + S0_b dS_c/2 + dS_b dS_c/3).
+// J_a = -(q w/V)(h_a/dt) cumsum_a W_a; 2D J3 = (q w/V) v3 W3.
+template <int NDIM, int SHAPE>
+__device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, const Pos& p0,
+                                        const Pos& p1, float* __restrict__ J) {
+    constexpr int K = Shape<SHAPE>::K;
+    constexpr int KW = K + 1;
+    float w0[K], w1[K];
+    float S0z[KW], DSz[KW], S0x[KW], DSx[KW], S0y[KW], DSy[KW];
+    int bz, bx, by = 0;
+    {
+        int b0 = p0.iz + Shape<SHAPE>::w(p0.oz, w0);
+        int b1 = p1.iz + Shape<SHAPE>::w(p1.oz, w1);
+        bz = min(b0, b1);
+        int s0 = b0 - bz, s1 = b1 - bz;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
+            float b = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
+            S0z[k] = a;
+            DSz[k] = b - a;
+        }
+    }
+    {
+        int b0 = p0.ix + Shape<SHAPE>::w(p0.ox, w0);
+        int b1 = p1.ix + Shape<SHAPE>::w(p1.ox, w1);
+        bx = min(b0, b1);
+        int s0 = b0 - bx, s1 = b1 - bx;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
+            float b = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
+            S0x[k] = a;
+            DSx[k] = b - a;
+        }
+    }
+    if (NDIM == 3) {
+        int b0 = p0.iy + Shape<SHAPE>::w(p0.oy, w0);
+        int b1 = p1.iy + Shape<SHAPE>::w(p1.oy, w1);
+        by = min(b0, b1);
+        int s0 = b0 - by, s1 = b1 - by;
+#pragma unroll
+        for (int k = 0; k < KW; ++k) {
+            float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
+            float b = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
+            S0y[k] = a;
+            DSy[k] = b - a;
+        }
+    }
+    const long long N = g.ncell;
+    const float f1 = -qv * g.dz / g.dt, f2 = -qv * g.dx / g.dt;
+    int gxs[KW];
+#pragma unroll
+    for (int k = 0; k < KW; ++k) gxs[k] = wrapi(bx + k, g.nx);
+
+    if (NDIM == 2) {
+        // J1: cumulative along z for each x row
+#pragma unroll
+        for (int b = 0; b < KW; ++b) {
+            float tx = S0x[b] + 0.5f * DSx[b];
+            long long row = (long long)gxs[b] * g.nz;
+            float cum = 0.f;
+#pragma unroll
+            for (int a = 0; a < KW - 1; ++a) {
+                cum += DSz[a] * tx;
+                int gz = bz + a;
+                if (gz >= 0 && gz < g.nz && cum != 0.f) atomicAdd(J + row + gz, f1 * cum);
+            }
+        }
+        // J2: cumulative along x for each z column; J3
+#pragma unroll
+        for (int a = 0; a < KW; ++a) {
+            int gz = bz + a;
+            if (gz < 0 || gz >= g.nz) continue;
+            float tz = S0z[a] + 0.5f * DSz[a];
+            float cum = 0.f;
+#pragma unroll
+            for (int b = 0; b < KW; ++b) {
+                long long o = (long long)gxs[b] * g.nz + gz;
+                if (b < KW - 1) {
+                    cum += DSx[b] * tz;
+                    if (cum != 0.f) atomicAdd(J + N + o, f2 * cum);
+                }
+                float w3 = S0z[a] * S0x[b] + 0.5f * DSz[a] * S0x[b] + 0.5f * S0z[a] * DSx[b]
+                         + (1.f / 3.f) * DSz[a] * DSx[b];
+                if (w3 != 0.f) atomicAdd(J + 2 * N + o, qv * v3 * w3);
+            }
+        }
+    } else {
+        const float f3 = -qv * g.dy / g.dt;
+        int gys[KW];
+#pragma unroll
+        for (int k = 0; k < KW; ++k) gys[k] = wrapi(by + k, g.ny);
+        // J1 along z
+#pragma unroll
+        for (int c = 0; c < KW; ++c)
+#pragma unroll
+            for (int b = 0; b < KW; ++b) {
+                float t = S0x[b] * S0y[c] + 0.5f * DSx[b] * S0y[c] + 0.5f * S0x[b] * DSy[c]
+                        + (1.f / 3.f) * DSx[b] * DSy[c];
+                long long row = ((long long)gys[c] * g.nx + gxs[b]) * g.nz;
+                float cum = 0.f;
+#pragma unroll
+                for (int a = 0; a < KW - 1; ++a) {
+                    cum += DSz[a] * t;
+                    int gz = bz + a;
+                    if (gz >= 0 && gz < g.nz && cum != 0.f) atomicAdd(J + row + gz, f1 * cum);
+                }
+            }
+        // J2 along x, J3 along y
+#pragma unroll
+        for (int a = 0; a < KW; ++a) {
+            int gz = bz + a;
+            if (gz < 0 || gz >= g.nz) continue;
+#pragma unroll
+            for (int c = 0; c < KW; ++c) {
+                float t = S0z[a] * S0y[c] + 0.5f * DSz[a] * S0y[c] + 0.5f * S0z[a] * DSy[c]
+                        + (1.f / 3.f) * DSz[a] * DSy[c];
+                float cum = 0.f;
+#pragma unroll
+                for (int b = 0; b < KW - 1; ++b) {
+                    cum += DSx[b] * t;
+                    long long o = ((long long)gys[c] * g.nx + gxs[b]) * g.nz + gz;
+                    if (cum != 0.f) atomicAdd(J + N + o, f2 * cum);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < KW; ++b) {
+                float t = S0z[a] * S0x[b] + 0.5f * DSz[a] * S0x[b] + 0.5f * S0z[a] * DSx[b]
+                        + (1.f / 3.f) * DSz[a] * DSx[b];
+                float cum = 0.f;
+#pragma unroll
+                for (int c = 0; c < KW - 1; ++c) {
+                    cum += DSy[c] * t;
+                    long long o = ((long long)gys[c] * g.nx + gxs[b]) * g.nz + gz;
+                    if (cum != 0.f) atomicAdd(J + 2 * N + o, f3 * cum);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- kernels ----
+enum { MODE_FUSED = 0, MODE_PUSH_ONLY = 1 };
+
+template <int NDIM, int SHAPE, int MODE>
+__device__ __forceinline__ void push_one(const GridP& g, const SpeciesP& sp, const float* __restrict__ E,
+                                         const float* __restrict__ B, float* __restrict__ J, int shift,
+                                         long long p, long long cap) {
+    int cell = sp.cell[p];
+    if (cell < 0) {
+        if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
+        return;
+    }
+    Pos p0;
+    int izg;
+    decode(g, cell, izg, p0.ix, p0.iy);
+    p0.iz = izg - 1 - shift;
+    if (p0.iz < 0 || p0.iz >= g.nz) {      // left through the back of the window (or stale)
+        sp.cell[p] = -1;
+        if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
+        return;
+    }
+    p0.oz = sp.off[p];
+    p0.ox = sp.off[cap + p];
+    p0.oy = NDIM == 3 ? sp.off[2 * cap + p] : 0.f;
+    float u[3] = {sp.u[p], sp.u[cap + p], sp.u[2 * cap + p]};
+
+    float eb[6];
+    gather<NDIM, SHAPE>(g, E, B, p0, eb);
+    boris(sp.eps, eb, u);
+
+    float gam = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    float ig = 1.f / gam;
+    Pos p1 = p0;
+    float mz = u[0] * ig * (g.dt / g.dz), mx = u[1] * ig * (g.dt / g.dx);
+    float my = NDIM == 3 ? u[2] * ig * (g.dt / g.dy) : 0.f;
+    // |v| < c and dt below the stability limit keep every move under one cell; anything else
+    // (a non-finite field or momentum) retires the particle instead of indexing outside.
+    if (!(fabsf(mz) < 1.f && fabsf(mx) < 1.f && fabsf(my) < 1.f)) {
+        sp.cell[p] = -1;
+        if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
+        return;
+    }
+    advance_axis(p1.iz, p1.oz, mz);
+    advance_axis(p1.ix, p1.ox, mx);
+    if (NDIM == 3) advance_axis(p1.iy, p1.oy, my);
+
+    if (MODE == MODE_FUSED) deposit<NDIM, SHAPE>(g, sp.qv, u[2] * ig, p0, p1, J);
+
+    int wx = wrapi(p1.ix, g.nx);
+    int wy = NDIM == 3 ? wrapi(p1.iy, g.ny) : 0;
+    if (MODE == MODE_PUSH_ONLY) {
+        sp.prev_cell[p] = encode(g, p0.iz, p0.ix, p0.iy);
+        sp.prev_off[p] = p0.oz;
+        sp.prev_off[cap + p] = p0.ox;
+        if (NDIM == 3) sp.prev_off[2 * cap + p] = p0.oy;
+        sp.cell[p] = encode(g, p1.iz, wx, wy);     // iz in [-1, nz]: guarded encoding
+    } else {
+        sp.cell[p] = (p1.iz >= 0 && p1.iz < g.nz) ? encode(g, p1.iz, wx, wy) : -1;
+    }
+    sp.off[p] = p1.oz;
+    sp.off[cap + p] = p1.ox;
+    if (NDIM == 3) sp.off[2 * cap + p] = p1.oy;
+    sp.u[p] = u[0];
+    sp.u[cap + p] = u[1];
+    sp.u[2 * cap + p] = u[2];
+}
+
+
+template <int NDIM, int SHAPE, int MODE>
+__global__ void __launch_bounds__(256) push_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
+                                                   const float* __restrict__ B, float* __restrict__ J,
+                                                   int shift) {
+    const long long n = *sp.count;
+    const long long cap = sp.cap;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        push_one<NDIM, SHAPE, MODE>(g, sp, E, B, J, shift, p, cap);
+}
+template <int NDIM, int SHAPE>
+__device__ __forceinline__ void deposit_one(const GridP& g, const SpeciesP& sp, float* __restrict__ J,
+                                            long long p) {
+    const long long cap = sp.cap;
+    int c0 = sp.prev_cell[p], c1 = sp.cell[p];
+    if (c0 < 0 || c1 < 0) return;
+    Pos p0, p1;
+    int izg;
+    decode(g, c0, izg, p0.ix, p0.iy);
+    p0.iz = izg - 1;
+    decode(g, c1, izg, p1.ix, p1.iy);
+    p1.iz = izg - 1;
+    // undo the periodic wrap of the new cell (moves are below one cell)
+    if (p1.ix - p0.ix > 1) p1.ix -= g.nx;
+    if (p1.ix - p0.ix < -1) p1.ix += g.nx;
+    if (NDIM == 3) {
+        if (p1.iy - p0.iy > 1) p1.iy -= g.ny;
+        if (p1.iy - p0.iy < -1) p1.iy += g.ny;
+    }
+    p0.oz = sp.prev_off[p];
+    p0.ox = sp.prev_off[cap + p];
+    p0.oy = NDIM == 3 ? sp.prev_off[2 * cap + p] : 0.f;
+    p1.oz = sp.off[p];
+    p1.ox = sp.off[cap + p];
+    p1.oy = NDIM == 3 ? sp.off[2 * cap + p] : 0.f;
+    float u0 = sp.u[p], u1 = sp.u[cap + p], u2 = sp.u[2 * cap + p];
+    float ig = 1.f / sqrtf(1.f + u0 * u0 + u1 * u1 + u2 * u2);
+    deposit<NDIM, SHAPE>(g, sp.qv, u2 * ig, p0, p1, J);
+    if (p1.iz < 0 || p1.iz >= g.nz) sp.cell[p] = -1;
+}
+
+// Unfused deposition from the positions saved by push_kernel<MODE_PUSH_ONLY>.
+template <int NDIM, int SHAPE>
+__global__ void __launch_bounds__(256) deposit_kernel(GridP g, SpeciesP sp, float* __restrict__ J) {
+    const long long n = *sp.count;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        deposit_one<NDIM, SHAPE>(g, sp, J, p);
+}
+
+// Cold plasma for the new front column, slot order (k, j, a, b, c) -> t.
+__global__ void inject_kernel(GridP g, SpeciesP sp, int pz, int px, int py, long long nnew,
+                              long long next_id, int* status) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnew) return;
+    long long base = *sp.count;
+    if (base + nnew > sp.cap) {
+        if (t == 0) atomicOr(status, STATUS_CAPACITY);
+        return;
+    }
+    long long r = t;
+    int c = (int)(r % py); r /= py;
+    int b = (int)(r % px); r /= px;
+    int a = (int)(r % pz); r /= pz;
+    int j = (int)(r % g.nx); r /= g.nx;
+    int k = (int)r;
+    long long s = base + t;
+    sp.cell[s] = encode(g, g.nz, j, k);   // iz = nz: the pending shift brings it to nz - 1
+    sp.off[s] = (a + 0.5f) / pz;
+    sp.off[sp.cap + s] = (b + 0.5f) / px;
+    if (g.ndim == 3) sp.off[2 * sp.cap + s] = (c + 0.5f) / py;
+    sp.u[s] = 0.f;
+    sp.u[sp.cap + s] = 0.f;
+    sp.u[2 * sp.cap + s] = 0.f;
+    if (sp.id) sp.id[s] = (int32_t)(next_id + t);
+}
+
+__global__ void add_count_kernel(int32_t* count, long long nnew, long long cap) {
+    if (*count + nnew <= cap) *count += (int32_t)nnew;
+}
+
+// ---- counting sort by cell ----
+__global__ void hist_kernel(SpeciesP sp, int32_t* hist) {
+    const long long n = *sp.count;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c = sp.cell[p];
+        if (c >= 0) atomicAdd(hist + c, 1);
+    }
+}
+
+constexpr int SCAN_T = 1024, SCAN_V = 4, SCAN_B = SCAN_T * SCAN_V;
+
+__device__ int block_exclusive_scan(int v, int* sw) {
+    // warp inclusive scan, then warp totals
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sw[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        sw[lane] = t;   // inclusive warp-total prefix
+    }
+    __syncthreads();
+    int before = wid > 0 ? sw[wid - 1] : 0;
+    int total = sw[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    sw[32] = total;
+    return before + x - v;
+}
+
+__global__ void __launch_bounds__(SCAN_T) scan_blocks_kernel(int32_t* a, long long n, int32_t* sums) {
+    __shared__ int sw[33];
+    long long base = (long long)blockIdx.x * SCAN_B + (long long)threadIdx.x * SCAN_V;
+    int v[SCAN_V];
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        v[k] = base + k < n ? a[base + k] : 0;
+        s += v[k];
+    }
+    int ex = block_exclusive_scan(s, sw);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SCAN_V; ++k) {
+        if (base + k < n) a[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = sw[32];
+}
+
+// exclusive scan of nb block sums in one block; sums[nb] receives the grand total
+__global__ void __launch_bounds__(SCAN_T) scan_sums_kernel(int32_t* sums, long long nb) {
+    __shared__ int sw[33];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base = 0; base < nb; base += SCAN_T) {
+        long long i = base + threadIdx.x;
+        int v = i < nb ? sums[i] : 0;
+        int ex = block_exclusive_scan(v, sw);
+        int c = carry;
+        if (i < nb) sums[i] = ex + c;
+        __syncthreads();
+        if (threadIdx.x == 0) carry = c + sw[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[nb] = carry;
+}
+
+__global__ void add_block_offsets_kernel(int32_t* a, long long n, const int32_t* sums) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] += sums[i / SCAN_B];
+}
+
+template <int NDIM>
+__global__ void scatter_kernel(SpeciesP sp, int32_t* cursor, int32_t* cell2, float* off2, float* u2,
+                               int32_t* id2) {
+    const long long n = *sp.count;
+    const long long cap = sp.cap;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        int c = sp.cell[p];
+        if (c < 0) continue;
+        long long d = atomicAdd(cursor + c, 1);
+        cell2[d] = c;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) off2[k * cap + d] = sp.off[k * cap + p];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u2[k * cap + d] = sp.u[k * cap + p];
+        if (id2) id2[d] = sp.id[p];
+    }
+}
+
+// copy the sorted slots [0, total) back into the caller's arrays and set the count
+template <int NDIM>
+__global__ void copy_back_kernel(SpeciesP sp, const int32_t* total, const int32_t* cell2, const float* off2,
+                                 const float* u2, const int32_t* id2) {
+    const long long n = *total;
+    const long long cap = sp.cap;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        sp.cell[p] = cell2[p];
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) sp.off[k * cap + p] = off2[k * cap + p];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sp.u[k * cap + p] = u2[k * cap + p];
+        if (id2) sp.id[p] = id2[p];
+    }
+}
+
+__global__ void set_count_kernel(int32_t* count, const int32_t* total) { *count = *total; }
+
+// ---- FP64 charge density at nodes ----
+template <int NDIM, int SHAPE>
+__device__ __forceinline__ void rho_one(const GridP& g, const SpeciesP& sp, int shift, double* rho,
+                                        long long p) {
+    int cell = sp.cell[p];
+    if (cell < 0) return;
+    int izg, ix, iy;
+    decode(g, cell, izg, ix, iy);
+    int iz = izg - 1 - shift;
+    if (iz < 0 || iz >= g.nz) return;
+    constexpr int K = Shape<SHAPE>::K;
+    double wz[K], wx[K], wy[K];
+    int bz = iz + Shape<SHAPE>::w((double)sp.off[p], wz);
+    int bx = ix + Shape<SHAPE>::w((double)sp.off[sp.cap + p], wx);
+    int by = NDIM == 3 ? iy + Shape<SHAPE>::w((double)sp.off[2 * sp.cap + p], wy) : 0;
+    for (int c = 0; c < (NDIM == 3 ? K : 1); ++c)
+        for (int b = 0; b < K; ++b)
+            for (int a = 0; a < K; ++a) {
+                int gz = bz + a;
+                if (gz < 0 || gz >= g.nz) continue;
+                int gx = wrapi(bx + b, g.nx);
+                int gy = NDIM == 3 ? wrapi(by + c, g.ny) : 0;
+                double w = wz[a] * wx[b] * (NDIM == 3 ? wy[c] : 1.0);
+                atomicAdd(rho + ((long long)gy * g.nx + gx) * g.nz + gz, sp.qv64 * w);
+            }
+}
+
+
+template <int NDIM, int SHAPE>
+__global__ void rho_kernel(GridP g, SpeciesP sp, int shift, double* rho) {
+    const long long n = *sp.count;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x)
+        rho_one<NDIM, SHAPE>(g, sp, shift, rho, p);
+}
+template <typename F>
+cudaError_t dispatch(int ndim, int shape, F&& f) {
+    if (ndim == 2 && shape == 1) return f(std::integral_constant<int, 2>(), std::integral_constant<int, 1>());
+    if (ndim == 2 && shape == 2) return f(std::integral_constant<int, 2>(), std::integral_constant<int, 2>());
+    if (ndim == 3 && shape == 1) return f(std::integral_constant<int, 3>(), std::integral_constant<int, 1>());
+    return f(std::integral_constant<int, 3>(), std::integral_constant<int, 2>());
+}
+
+inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+// grid-stride kernels: enough CTAs for the expected extent, at most 16 per SM of a 152-SM part
+inline unsigned pblocks(long long extent) {
+    long long b = (extent + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+}  // namespace
+
+cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, const float* B, float* J,
+                        int shift, int mode, long long extent, cudaStream_t s) {
+    if (extent <= 0) return cudaSuccess;
+    return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
+        constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
+        if (mode == MODE_FUSED)
+            push_kernel<ND, SH, MODE_FUSED><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, J, shift);
+        else
+            push_kernel<ND, SH, MODE_PUSH_ONLY><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, J, shift);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J, long long extent,
+                                   cudaStream_t s) {
+    if (extent <= 0) return cudaSuccess;
+    return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
+        constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
+        deposit_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, J);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], long long next_id,
+                          int* status, cudaStream_t s) {
+    int pz = ppc[0], px = ppc[1], py = g.ndim == 3 ? ppc[2] : 1;
+    long long nnew = (long long)g.nx * (g.ndim == 3 ? g.ny : 1) * pz * px * py;
+    if (nnew <= 0) return cudaSuccess;
+    inject_kernel<<<nblocks(nnew, 256), 256, 0, s>>>(g, sp, pz, px, py, nnew, next_id, status);
+    add_count_kernel<<<1, 1, 0, s>>>(sp.count, nnew, sp.cap);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort(const GridP& g, const SpeciesP& sp, long long extent, int32_t* hist,
+                        int32_t* blocksums, int32_t* cell_alt, float* off_alt, float* u_alt,
+                        int32_t* id_alt, cudaStream_t s) {
+    if (extent <= 0) return cudaSuccess;
+    const long long nb = (long long)g.nzg * g.nx * g.ny;
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * nb, s);
+    if (e != cudaSuccess) return e;
+    hist_kernel<<<pblocks(extent), 256, 0, s>>>(sp, hist);
+    long long nblk = (nb + SCAN_B - 1) / SCAN_B;
+    scan_blocks_kernel<<<(unsigned)nblk, SCAN_T, 0, s>>>(hist, nb, blocksums);
+    scan_sums_kernel<<<1, SCAN_T, 0, s>>>(blocksums, nblk);
+    add_block_offsets_kernel<<<nblocks(nb, 256), 256, 0, s>>>(hist, nb, blocksums);
+    if (g.ndim == 2)
+        scatter_kernel<2><<<pblocks(extent), 256, 0, s>>>(sp, hist, cell_alt, off_alt, u_alt,
+                                                               sp.id ? id_alt : nullptr);
+    else
+        scatter_kernel<3><<<pblocks(extent), 256, 0, s>>>(sp, hist, cell_alt, off_alt, u_alt,
+                                                               sp.id ? id_alt : nullptr);
+    if (g.ndim == 2)
+        copy_back_kernel<2><<<pblocks(extent), 256, 0, s>>>(sp, blocksums + nblk, cell_alt, off_alt, u_alt,
+                                                             sp.id ? id_alt : nullptr);
+    else
+        copy_back_kernel<3><<<pblocks(extent), 256, 0, s>>>(sp, blocksums + nblk, cell_alt, off_alt, u_alt,
+                                                             sp.id ? id_alt : nullptr);
+    set_count_kernel<<<1, 1, 0, s>>>(sp.count, blocksums + nblk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rho(const GridP& g, const SpeciesP& sp, int shift, double* rho, long long extent,
+                       cudaStream_t s) {
+    if (extent <= 0) return cudaSuccess;
+    return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
+        constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
+        rho_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, shift, rho);
+        return cudaGetLastError();
+    });
+}
+
+}  // namespace pic

@@ -1,0 +1,647 @@
+// C ABI of libpic (include/pic.h): handle lifecycle, validation, scratch ownership and the
+// ordering of the kernels that make up one PIC step (Sec. 1 loop of arXiv:1910.13529).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pic_internal.h"
+
+using namespace pic;
+
+struct SpeciesSlot {
+    bool bound = false;
+    int32_t* cell = nullptr;
+    float* off = nullptr;
+    float* u = nullptr;
+    int32_t* id = nullptr;
+    long long cap = 0;
+    long long extent = 0;      // upper bound of the device count
+    double q = 0, m = 1, w = 0;
+    int32_t* prev_cell = nullptr;   // library scratch for the unfused path
+    float* prev_off = nullptr;
+};
+
+struct pic_t {
+    pic_config cfg;
+    GridP g;
+    StencilP st;
+    double C64[PIC_MAX_M];
+    double h64[2 * PIC_MAX_HLEN + 1];
+    float hf[2 * PIC_MAX_HLEN + 1];
+    int hlen = 0;
+    int device = 0;
+    float* E = nullptr;
+    float* B = nullptr;
+    float* J = nullptr;
+    // scratch owned by the library
+    float* E2 = nullptr;
+    float* B2 = nullptr;
+    double* rho64 = nullptr;
+    double* acc = nullptr;
+    int* status = nullptr;
+    int32_t* counts = nullptr;
+    int32_t* hist = nullptr;
+    int32_t* blocksums = nullptr;
+    int32_t* cell_alt = nullptr;
+    float* off_alt = nullptr;
+    float* u_alt = nullptr;
+    int32_t* id_alt = nullptr;
+    long long alt_cap = 0;
+    SpeciesSlot sp[PIC_MAX_SPECIES];
+    long long step = 0, shifts = 0, next_id = 0;
+    int pending_shift = 0;
+    int state = 0;   // 0: idle, 1: pushed (unfused), 2: deposited
+    char err[256] = {0};
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_a, ev_b;
+    std::vector<int> ev_cat;
+    size_t ev_used = 0;
+    long long launches[PIC_TIMING_N] = {0};
+};
+
+namespace {
+
+char g_create_err[256] = "no error";
+
+pic_status fail(pic_t* h, pic_status st, const char* fmt, ...) {
+    char* dst = h ? h->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pic_status cuda_fail(pic_t* h, cudaError_t e, const char* what) {
+    return fail(h, PIC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call, what)                                  \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+template <typename T>
+pic_status dalloc(pic_t* h, T** p, size_t n, const char* what) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(h, PIC_ERR_OOM, "cudaMalloc %s (%zu bytes): %s", what, sizeof(T) * n, cudaGetErrorString(e));
+    }
+    return PIC_OK;
+}
+
+void dfree(void* p) {
+    if (p) cudaFree(p);
+}
+
+// Brackets one kernel class on the stream with a pair of events while timing is on.
+struct Scope {
+    pic_t* h;
+    cudaStream_t s;
+    size_t i;
+    bool on;
+    Scope(pic_t* h_, int cat, int nlaunch, cudaStream_t s_) : h(h_), s(s_), i(0), on(h_->timing) {
+        h->launches[cat] += nlaunch;
+        if (!on) return;
+        if (h->ev_used == h->ev_a.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+                on = false;
+                return;
+            }
+            h->ev_a.push_back(a);
+            h->ev_b.push_back(b);
+            h->ev_cat.push_back(cat);
+        }
+        i = h->ev_used++;
+        h->ev_cat[i] = cat;
+        cudaEventRecord(h->ev_a[i], s);
+    }
+    ~Scope() {
+        if (on) cudaEventRecord(h->ev_b[i], s);
+    }
+};
+
+SpeciesP species_params(pic_t* h, int s) {
+    SpeciesSlot& q = h->sp[s];
+    SpeciesP p;
+    p.cell = q.cell;
+    p.off = q.off;
+    p.u = q.u;
+    p.id = q.id;
+    p.count = h->counts + s;
+    p.cap = q.cap;
+    double V = h->cfg.dz * h->cfg.dx * (h->cfg.ndim == 3 ? h->cfg.dy : 1.0);
+    p.eps = (float)(q.q * h->cfg.dt / (2.0 * q.m));
+    p.qv64 = q.q * q.w / V;
+    p.qv = (float)p.qv64;
+    p.wm = q.w * q.m;
+    p.prev_cell = q.prev_cell;
+    p.prev_off = q.prev_off;
+    return p;
+}
+
+bool window_due(const pic_t* h, long long steps_done) {
+    if (!h->cfg.moving_window) return false;
+    return (long long)std::floor(steps_done * h->cfg.dt / h->cfg.dz + 1e-9) > h->shifts;
+}
+
+pic_status need_fields(pic_t* h) {
+    if (!h->E || !h->B || !h->J) return fail(h, PIC_ERR_STATE, "fields not bound (pic_bind_fields)");
+    return PIC_OK;
+}
+
+// Field advance from (Ein, Bin) into (Eout, Bout), with the window shift and injection that
+// complete step n.  J1 has already been corrected in place for the customised stencil.
+pic_status advance_fields(pic_t* h, const float* Ein, const float* Bin, float* Eout, float* Bout,
+                          cudaStream_t s) {
+    const long long N = h->g.ncell;
+    const long long n_done = h->step + 1;
+    const int shift = window_due(h, n_done) ? 1 : 0;
+    FieldP p;
+    p.g = h->g;
+    p.st = h->st;
+    p.Ein = Ein;
+    p.Bin = Bin;
+    p.J1 = h->J;
+    p.J2 = h->J + N;
+    p.J3 = h->J + 2 * N;
+    p.Eout = Eout;
+    p.Bout = Bout;
+    p.shift = shift;
+    {
+        Scope sc(h, PIC_T_FIELDS, 1, s);
+        CK(h, launch_field_advance(p, s), "field advance kernel");
+    }
+    h->step = n_done;
+    if (shift) {
+        h->shifts += 1;
+        h->pending_shift = 1;
+        int is = h->cfg.inject_species;
+        if (is >= 0 && h->sp[is].bound) {
+            SpeciesP sp = species_params(h, is);
+            {
+                Scope sc(h, PIC_T_WINDOW, 2, s);
+                CK(h, launch_inject(h->g, sp, h->cfg.inject_ppc, h->next_id, h->status, s), "inject kernel");
+            }
+            long long nnew = (long long)h->cfg.nx * (h->cfg.ndim == 3 ? h->cfg.ny : 1) * h->cfg.inject_ppc[0] *
+                             h->cfg.inject_ppc[1] * (h->cfg.ndim == 3 ? h->cfg.inject_ppc[2] : 1);
+            h->next_id += nnew;
+            long long ext = h->sp[is].extent + nnew;
+            h->sp[is].extent = ext < h->sp[is].cap ? ext : h->sp[is].cap;
+        }
+    }
+    return PIC_OK;
+}
+
+pic_status ensure_sort_scratch(pic_t* h) {
+    long long cap = 0;
+    bool ids = false;
+    for (auto& q : h->sp)
+        if (q.bound) {
+            cap = q.cap > cap ? q.cap : cap;
+            ids = ids || q.id;
+        }
+    if (!h->hist) {
+        long long nb = (long long)h->g.nzg * h->g.nx * h->g.ny;
+        pic_status st = dalloc(h, &h->hist, nb, "sort histogram");
+        if (st) return st;
+        if ((st = dalloc(h, &h->blocksums, nb / 4096 + 16, "sort block sums"))) return st;
+    }
+    if (cap > h->alt_cap) {
+        dfree(h->cell_alt);
+        dfree(h->off_alt);
+        dfree(h->u_alt);
+        dfree(h->id_alt);
+        h->cell_alt = nullptr;
+        h->off_alt = h->u_alt = nullptr;
+        h->id_alt = nullptr;
+        h->alt_cap = 0;
+        pic_status st;
+        if ((st = dalloc(h, &h->cell_alt, cap, "sort cells"))) return st;
+        if ((st = dalloc(h, &h->off_alt, cap * h->cfg.ndim, "sort offsets"))) return st;
+        if ((st = dalloc(h, &h->u_alt, cap * 3, "sort momenta"))) return st;
+        if ((st = dalloc(h, &h->id_alt, cap, "sort ids"))) return st;
+        h->alt_cap = cap;
+    }
+    return PIC_OK;
+}
+
+pic_status do_sort(pic_t* h, cudaStream_t s) {
+    pic_status st = ensure_sort_scratch(h);
+    if (st) return st;
+    for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+        if (!h->sp[i].bound) continue;
+        SpeciesP sp = species_params(h, i);
+        // the alternate arrays use the species' own capacity as component stride
+        Scope sc(h, PIC_T_SORT, 8, s);
+        CK(h, launch_sort(h->g, sp, h->sp[i].extent, h->hist, h->blocksums, h->cell_alt, h->off_alt,
+                          h->u_alt, h->id_alt, s),
+           "sort kernels");
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pic_last_error(const pic_t* h) { return h ? h->err : g_create_err; }
+
+pic_status pic_fit_coefficients(double kappa, int M, double wk, double n, double* C_out) {
+    if (!C_out || M < 1 || M > PIC_MAX_M || !(kappa > 0.0)) return PIC_ERR_ARG;
+    return fit_coefficients(kappa, M, wk, n, C_out) ? PIC_ERR_ARG : PIC_OK;
+}
+
+pic_status pic_correction_taps(const double* C, int M, int hlen, double* h_out) {
+    if (!C || !h_out || M < 1 || M > PIC_MAX_M || hlen < 0 || hlen > 4096) return PIC_ERR_ARG;
+    return correction_taps(C, M, hlen, h_out) ? PIC_ERR_ARG : PIC_OK;
+}
+
+pic_status pic_cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M, double* dt_out) {
+    if (!dt_out || !C || M < 1 || M > PIC_MAX_M || (ndim != 2 && ndim != 3) || !(dz > 0) || !(dx > 0) ||
+        (ndim == 3 && !(dy > 0)))
+        return PIC_ERR_ARG;
+    *dt_out = cfl_dt(ndim, dz, dx, dy, C, M);
+    return PIC_OK;
+}
+
+pic_status pic_create(const pic_config* cfg, pic_t** out) {
+    if (!cfg || !out) return fail(nullptr, PIC_ERR_ARG, "null argument");
+    *out = nullptr;
+    const pic_config& c = *cfg;
+    if (c.ndim != 2 && c.ndim != 3) return fail(nullptr, PIC_ERR_ARG, "ndim must be 2 or 3");
+    int ny = c.ndim == 3 ? c.ny : 1;
+    if (c.nz < 4 || c.nx < 4 || (c.ndim == 3 && c.ny < 4))
+        return fail(nullptr, PIC_ERR_ARG, "grid too small (nz, nx, ny >= 4)");
+    if ((long long)(c.nz + 2) * c.nx * ny >= (1LL << 31) - 1)
+        return fail(nullptr, PIC_ERR_ARG, "grid too large for 32-bit cell indices");
+    if (c.nz > 32768) return fail(nullptr, PIC_ERR_ARG, "nz above 32768");
+    if (!(c.dz > 0) || !(c.dx > 0) || (c.ndim == 3 && !(c.dy > 0)) || !(c.dt > 0))
+        return fail(nullptr, PIC_ERR_ARG, "cell sizes and dt must be positive");
+    if (c.solver != PIC_SOLVER_YEE && c.solver != PIC_SOLVER_CUSTOM)
+        return fail(nullptr, PIC_ERR_ARG, "unknown solver %d", c.solver);
+    if (c.shape != 1 && c.shape != 2) return fail(nullptr, PIC_ERR_ARG, "shape must be 1 or 2");
+    if (c.inject_species >= PIC_MAX_SPECIES) return fail(nullptr, PIC_ERR_ARG, "inject_species out of range");
+    if (c.inject_species >= 0 && (c.inject_ppc[0] < 1 || c.inject_ppc[1] < 1 || (c.ndim == 3 && c.inject_ppc[2] < 1)))
+        return fail(nullptr, PIC_ERR_ARG, "inject_ppc must be >= 1");
+    int M = 1;
+    double C[PIC_MAX_M] = {1.0};
+    if (c.solver == PIC_SOLVER_CUSTOM) {
+        M = c.M;
+        if (M < 1 || M > PIC_MAX_M) return fail(nullptr, PIC_ERR_ARG, "M must be in [1, %d]", PIC_MAX_M);
+        if (c.coef) {
+            for (int l = 0; l < M; ++l) C[l] = c.coef[l];
+        } else if (fit_coefficients(c.dz / c.dt, M, c.fit_wk, c.fit_n, C)) {
+            return fail(nullptr, PIC_ERR_ARG, "coefficient fit failed");
+        }
+    }
+    double dtmax = cfl_dt(c.ndim, c.dz, c.dx, c.dy, C, M);
+    if (c.dt > dtmax * (1.0 + 1e-12))
+        return fail(nullptr, PIC_ERR_CFL, "dt = %.6g above the stability limit %.6g", c.dt, dtmax);
+
+    pic_t* h = new (std::nothrow) pic_t();
+    if (!h) return fail(nullptr, PIC_ERR_OOM, "host allocation");
+    h->cfg = c;
+    h->cfg.ny = ny;
+    h->cfg.coef = nullptr;
+    if (c.ndim == 2) h->cfg.dy = 1.0;
+    cudaGetDevice(&h->device);
+    GridP& g = h->g;
+    g.ndim = c.ndim;
+    g.nz = c.nz;
+    g.nx = c.nx;
+    g.ny = ny;
+    g.nzg = c.nz + 2;
+    g.ncell = (long long)c.nz * c.nx * ny;
+    g.dz = (float)c.dz;
+    g.dx = (float)c.dx;
+    g.dy = (float)h->cfg.dy;
+    g.dt = (float)c.dt;
+    g.shape = c.shape;
+    h->st.M = M;
+    for (int l = 0; l < PIC_MAX_M; ++l) {
+        h->C64[l] = l < M ? C[l] : 0.0;
+        h->st.C[l] = (float)h->C64[l];
+    }
+    if (c.solver == PIC_SOLVER_CUSTOM && M > 1) {
+        h->hlen = PIC_MAX_HLEN;
+        if (correction_taps(C, M, h->hlen, h->h64)) {
+            delete h;
+            return fail(nullptr, PIC_ERR_ARG, "stencil symbol ratio has a zero: no current correction");
+        }
+        for (int i = 0; i < 2 * h->hlen + 1; ++i) h->hf[i] = (float)h->h64[i];
+    }
+    const long long N = g.ncell;
+    pic_status st;
+    if ((st = dalloc(h, &h->E2, 3 * N, "field buffer E")) || (st = dalloc(h, &h->B2, 3 * N, "field buffer B")) ||
+        (st = dalloc(h, &h->rho64, N, "rho")) || (st = dalloc(h, &h->acc, 16, "diag accumulators")) ||
+        (st = dalloc(h, &h->status, 1, "status")) || (st = dalloc(h, &h->counts, PIC_MAX_SPECIES, "counts"))) {
+        snprintf(g_create_err, sizeof g_create_err, "%s", h->err);
+        pic_destroy(h);
+        return st;
+    }
+    cudaError_t e = cudaMemset(h->status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->counts, 0, sizeof(int32_t) * PIC_MAX_SPECIES);
+    if (e != cudaSuccess) {
+        snprintf(g_create_err, sizeof g_create_err, "cudaMemset: %s", cudaGetErrorString(e));
+        pic_destroy(h);
+        return PIC_ERR_CUDA;
+    }
+    *out = h;
+    return PIC_OK;
+}
+
+pic_status pic_destroy(pic_t* h) {
+    if (!h) return PIC_OK;
+    void* ptrs[] = {h->E2, h->B2, h->rho64, h->acc, h->status, h->counts, h->hist, h->blocksums,
+                    h->cell_alt, h->off_alt, h->u_alt, h->id_alt};
+    for (void* p : ptrs) dfree(p);
+    for (size_t i = 0; i < h->ev_a.size(); ++i) {
+        cudaEventDestroy(h->ev_a[i]);
+        cudaEventDestroy(h->ev_b[i]);
+    }
+    for (auto& q : h->sp) {
+        dfree(q.prev_cell);
+        dfree(q.prev_off);
+    }
+    delete h;
+    return PIC_OK;
+}
+
+pic_status pic_get_coefficients(const pic_t* h, double* C_out, int* M, double* h_out, int* hlen) {
+    if (!h) return PIC_ERR_ARG;
+    if (C_out)
+        for (int l = 0; l < PIC_MAX_M; ++l) C_out[l] = h->C64[l];
+    if (M) *M = h->st.M;
+    if (h_out)
+        for (int i = 0; i < 2 * PIC_MAX_HLEN + 1; ++i) h_out[i] = i < 2 * h->hlen + 1 ? h->h64[i] : 0.0;
+    if (hlen) *hlen = h->hlen;
+    return PIC_OK;
+}
+
+pic_status pic_bind_fields(pic_t* h, float* E, float* B, float* J) {
+    if (!h) return PIC_ERR_ARG;
+    if (!E || !B || !J) return fail(h, PIC_ERR_ARG, "null field pointer");
+    h->E = E;
+    h->B = B;
+    h->J = J;
+    return PIC_OK;
+}
+
+pic_status pic_bind_species(pic_t* h, int s, int32_t* cell, float* off, float* u, int32_t* id, int64_t n,
+                            int64_t cap, double q, double m, double w) {
+    if (!h) return PIC_ERR_ARG;
+    if (s < 0 || s >= PIC_MAX_SPECIES) return fail(h, PIC_ERR_ARG, "species index %d out of range", s);
+    if (!cell || !off || !u) return fail(h, PIC_ERR_ARG, "null particle pointer");
+    if (n < 0 || cap < n || cap > (1LL << 31) - 1) return fail(h, PIC_ERR_ARG, "need 0 <= n <= cap < 2^31");
+    if (!(m > 0)) return fail(h, PIC_ERR_ARG, "mass must be positive");
+    SpeciesSlot& sl = h->sp[s];
+    dfree(sl.prev_cell);
+    dfree(sl.prev_off);
+    sl = SpeciesSlot();
+    sl.bound = true;
+    sl.cell = cell;
+    sl.off = off;
+    sl.u = u;
+    sl.id = id;
+    sl.cap = cap;
+    sl.extent = n;
+    sl.q = q;
+    sl.m = m;
+    sl.w = w;
+    int32_t n32 = (int32_t)n;
+    CK(h, cudaMemcpy(h->counts + s, &n32, sizeof(int32_t), cudaMemcpyHostToDevice), "count upload");
+    if (id && h->next_id < n) h->next_id = n;
+    return PIC_OK;
+}
+
+pic_status pic_gather_push(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+        SpeciesSlot& q = h->sp[i];
+        if (!q.bound) continue;
+        if (!q.prev_cell) {
+            if ((st = dalloc(h, &q.prev_cell, q.cap, "previous cells"))) return st;
+            if ((st = dalloc(h, &q.prev_off, q.cap * h->cfg.ndim, "previous offsets"))) return st;
+        }
+        SpeciesP sp = species_params(h, i);
+        Scope sc(h, PIC_T_PARTICLES, 1, s);
+        CK(h, launch_push(h->g, sp, h->E, h->B, nullptr, h->pending_shift, 1, q.extent, s), "push kernel");
+    }
+    h->pending_shift = 0;
+    h->state = 1;
+    return PIC_OK;
+}
+
+pic_status pic_deposit(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    if (h->state != 1) return fail(h, PIC_ERR_STATE, "pic_deposit needs a preceding pic_gather_push");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = h->g.ncell;
+    {
+        Scope sc(h, PIC_T_DEPOSIT, 1, s);
+        CK(h, cudaMemsetAsync(h->J, 0, sizeof(float) * 3 * N, s), "zero J");
+    }
+    for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+        if (!h->sp[i].bound) continue;
+        SpeciesP sp = species_params(h, i);
+        Scope sc(h, PIC_T_DEPOSIT, 1, s);
+        CK(h, launch_deposit_unfused(h->g, sp, h->J, h->sp[i].extent, s), "deposit kernel");
+    }
+    if (h->hlen > 0) {
+        Scope sc(h, PIC_T_CORRECTION, 1, s);
+        CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
+    }
+    h->state = 2;
+    return PIC_OK;
+}
+
+pic_status pic_field_advance(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = h->g.ncell;
+    if ((st = advance_fields(h, h->E, h->B, h->E2, h->B2, s))) return st;
+    Scope sc(h, PIC_T_FIELDS, 2, s);
+    CK(h, cudaMemcpyAsync(h->E, h->E2, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy E");
+    CK(h, cudaMemcpyAsync(h->B, h->B2, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy B");
+    h->state = 0;
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_t* h, int nsteps, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    if (nsteps < 0) return fail(h, PIC_ERR_ARG, "nsteps < 0");
+    pic_status st = need_fields(h);
+    if (st) return st;
+    if (h->state == 1) return fail(h, PIC_ERR_STATE, "pic_step after pic_gather_push without pic_deposit");
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = h->g.ncell;
+    float *Ec = h->E, *Bc = h->B, *En = h->E2, *Bn = h->B2;
+    for (int it = 0; it < nsteps; ++it) {
+        if (h->cfg.sort_every > 0 && h->step % h->cfg.sort_every == 0)
+            if ((st = do_sort(h, s))) return st;
+        {
+            Scope sc(h, PIC_T_DEPOSIT, 1, s);
+            CK(h, cudaMemsetAsync(h->J, 0, sizeof(float) * 3 * N, s), "zero J");
+        }
+        for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+            if (!h->sp[i].bound) continue;
+            SpeciesP sp = species_params(h, i);
+            Scope sc(h, PIC_T_PARTICLES, 1, s);
+            CK(h, launch_push(h->g, sp, Ec, Bc, h->J, h->pending_shift, 0, h->sp[i].extent, s),
+               "fused push/deposit kernel");
+        }
+        h->pending_shift = 0;
+        if (h->hlen > 0) {
+            Scope sc(h, PIC_T_CORRECTION, 1, s);
+            CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
+        }
+        if ((st = advance_fields(h, Ec, Bc, En, Bn, s))) return st;
+        float* t = Ec;
+        Ec = En;
+        En = t;
+        t = Bc;
+        Bc = Bn;
+        Bn = t;
+    }
+    if (Ec != h->E) {
+        Scope sc(h, PIC_T_FIELDS, 2, s);
+        CK(h, cudaMemcpyAsync(h->E, Ec, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy E");
+        CK(h, cudaMemcpyAsync(h->B, Bc, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy B");
+    }
+    h->state = 0;
+    return PIC_OK;
+}
+
+pic_status pic_sort(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    if (h->state == 1) return fail(h, PIC_ERR_STATE, "pic_sort between pic_gather_push and pic_deposit");
+    return do_sort(h, (cudaStream_t)stream);
+}
+
+pic_status pic_rho(pic_t* h, double* rho, void* stream) {
+    if (!h || !rho) return PIC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(h, cudaMemsetAsync(rho, 0, sizeof(double) * h->g.ncell, s), "zero rho");
+    for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+        if (!h->sp[i].bound) continue;
+        SpeciesP sp = species_params(h, i);
+        CK(h, launch_rho(h->g, sp, h->pending_shift, rho, h->sp[i].extent, s), "rho kernel");
+    }
+    return PIC_OK;
+}
+
+pic_status pic_gauss(pic_t* h, double* G, void* stream) {
+    if (!h || !G) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    if ((st = pic_rho(h, h->rho64, stream))) return st;
+    CK(h, launch_gauss(h->g, h->st, h->E, h->rho64, h->cfg.rho_bg, G, (cudaStream_t)stream), "gauss kernel");
+    return PIC_OK;
+}
+
+pic_status pic_diag(pic_t* h, double* out, void* stream) {
+    if (!h || !out) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scope sc(h, PIC_T_DIAG, 3, s);
+    if ((st = pic_rho(h, h->rho64, stream))) return st;
+    CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * 16, s), "zero accumulators");
+    int margin = h->hlen > 0 ? h->st.M + h->hlen + 2 : 2;
+    CK(h, launch_diag_reduce(h->g, h->st, h->E, h->B, h->rho64, h->cfg.rho_bg, margin, h->acc, s), "diag kernel");
+    for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+        if (!h->sp[i].bound) continue;
+        SpeciesP sp = species_params(h, i);
+        CK(h, launch_kinetic(h->g, sp, h->sp[i].extent, h->acc, s), "kinetic kernel");
+    }
+    double acc[16];
+    int status = 0;
+    CK(h, cudaMemcpyAsync(acc, h->acc, sizeof acc, cudaMemcpyDeviceToHost, s), "read accumulators");
+    CK(h, cudaMemcpyAsync(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost, s), "read status");
+    CK(h, cudaStreamSynchronize(s), "diag synchronise");
+    double V = h->cfg.dz * h->cfg.dx * h->cfg.dy;
+    out[PIC_DIAG_GAUSS_MAX] = acc[0];
+    out[PIC_DIAG_GAUSS_RMS] = acc[5] > 0 ? std::sqrt(acc[1] / acc[5]) : 0.0;
+    out[PIC_DIAG_RHO_MAX] = acc[2];
+    out[PIC_DIAG_FIELD_ENERGY] = 0.5 * acc[3] * V;
+    out[PIC_DIAG_KINETIC] = acc[4];
+    out[PIC_DIAG_COUNT] = acc[6];
+    out[PIC_DIAG_STEP] = (double)h->step;
+    out[PIC_DIAG_SHIFTS] = (double)h->shifts;
+    out[PIC_DIAG_STATUS] = (double)status;
+    out[PIC_DIAG_INTERIOR] = acc[5];
+    if (status & STATUS_CAPACITY) return fail(h, PIC_ERR_CAPACITY, "particle capacity exceeded during injection");
+    return PIC_OK;
+}
+
+pic_status pic_get_count(pic_t* h, int s, int64_t* n, void* stream) {
+    if (!h || !n || s < 0 || s >= PIC_MAX_SPECIES) return PIC_ERR_ARG;
+    int32_t c = 0;
+    CK(h, cudaMemcpyAsync(&c, h->counts + s, sizeof c, cudaMemcpyDeviceToHost, (cudaStream_t)stream), "read count");
+    CK(h, cudaStreamSynchronize((cudaStream_t)stream), "count synchronise");
+    *n = c;
+    return PIC_OK;
+}
+
+pic_status pic_get_state(const pic_t* h, int64_t* step, int64_t* shifts, int* pending_shift) {
+    if (!h) return PIC_ERR_ARG;
+    if (step) *step = h->step;
+    if (shifts) *shifts = h->shifts;
+    if (pending_shift) *pending_shift = h->pending_shift;
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    CK(h, cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
+    int status = 0;
+    CK(h, cudaMemcpy(&status, h->status, sizeof(int), cudaMemcpyDeviceToHost), "read status");
+    if (status & STATUS_CAPACITY) return fail(h, PIC_ERR_CAPACITY, "particle capacity exceeded during injection");
+    return PIC_OK;
+}
+
+pic_status pic_timing(pic_t* h, int enable) {
+    if (!h) return PIC_ERR_ARG;
+    if (enable) {
+        h->ev_used = 0;
+        for (auto& c : h->launches) c = 0;
+    }
+    h->timing = enable != 0;
+    return PIC_OK;
+}
+
+pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    CK(h, cudaStreamSynchronize((cudaStream_t)stream), "timing synchronise");
+    double acc[PIC_TIMING_N] = {0};
+    for (size_t i = 0; i < h->ev_used; ++i) {
+        float t = 0.f;
+        CK(h, cudaEventElapsedTime(&t, h->ev_a[i], h->ev_b[i]), "event time");
+        acc[h->ev_cat[i]] += t;
+    }
+    for (int c = 0; c < PIC_TIMING_N; ++c) {
+        if (ms) ms[c] = acc[c];
+        if (launches) launches[c] = h->launches[c];
+    }
+    return PIC_OK;
+}
+
+}  // extern "C"

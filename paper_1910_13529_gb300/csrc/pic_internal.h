@@ -1,0 +1,87 @@
+// Internal declarations shared by the CUDA translation units of libpic.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// Grid constants passed by value to every kernel.
+struct GridP {
+    int ndim;
+    int nz, nx, ny;     // cells
+    int nzg;            // nz + 2: z extent of the guarded particle cell index
+    long long ncell;    // nz * nx * ny
+    float dz, dx, dy, dt;
+    int shape;          // 1 or 2
+};
+
+// Axial stencil (Appendix C).  M = 1, C[0] = 1 is the Yee difference.
+struct StencilP {
+    int M;
+    float C[PIC_MAX_M];
+};
+
+// Field-advance launch parameters.
+struct FieldP {
+    GridP g;
+    StencilP st;
+    const float* Ein;
+    const float* Bin;
+    const float* J1;     // current components (J1 may be the corrected copy)
+    const float* J2;
+    const float* J3;
+    float* Eout;
+    float* Bout;
+    int shift;           // 1: write the result one cell towards -z, zero the front column
+};
+
+// One species' particle arrays and per-species constants.
+struct SpeciesP {
+    int32_t* cell;
+    float* off;          // [ndim][cap]
+    float* u;            // [3][cap]
+    int32_t* id;         // may be null
+    int32_t* count;      // device live-slot extent
+    long long cap;
+    float eps;           // q dt / (2 m)   (Boris)
+    float qv;            // q w / V        (charge density of one macro-particle per unit shape)
+    double qv64;
+    double wm;           // w m            (kinetic energy)
+    int32_t* prev_cell;  // scratch for the unfused path
+    float* prev_off;
+};
+
+// Device status word bits.
+enum : int { STATUS_CAPACITY = 1, STATUS_TIMEOUT = 2 };
+
+// ---- launchers (return cudaGetLastError of the launch) ----
+cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s);
+cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s);
+cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, const float* B,
+                        float* J, int shift, int mode, long long extent, cudaStream_t s);
+cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J, long long extent,
+                                   cudaStream_t s);
+cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], long long next_id,
+                          int* status, cudaStream_t s);
+cudaError_t launch_sort(const GridP& g, const SpeciesP& sp, long long extent, int32_t* hist,
+                        int32_t* blocksums, int32_t* cell_alt, float* off_alt, float* u_alt,
+                        int32_t* id_alt, cudaStream_t s);
+cudaError_t launch_rho(const GridP& g, const SpeciesP& sp, int shift, double* rho, long long extent,
+                       cudaStream_t s);
+cudaError_t launch_gauss(const GridP& g, const StencilP& st, const float* E, const double* rho,
+                         double rho_bg, double* G, cudaStream_t s);
+cudaError_t launch_diag_reduce(const GridP& g, const StencilP& st, const float* E, const float* B,
+                               const double* rho, double rho_bg, int margin, double* acc,
+                               cudaStream_t s);
+cudaError_t launch_kinetic(const GridP& g, const SpeciesP& sp, long long extent, double* acc,
+                           cudaStream_t s);
+
+// ---- host math (host_math.cpp) ----
+int fit_coefficients(double kappa, int M, double wk, double n, double* C);
+int correction_taps(const double* C, int M, int hlen, double* h);
+double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M);
+
+}  // namespace pic
