@@ -2,8 +2,8 @@
 
 Thin ctypes marshalling over the C ABI in include/pic.h: the functions below carry the C
 names and arguments; every step of the PIC loop runs in the CUDA kernels of csrc/.  PyTorch
-is used only for device memory and streams (see runtime.py).  Importing this module raises
-if the compiled library is missing -- there is no CPU fallback.
+is used only for device memory and streams (see runtime.py).  The first call raises
+ImportError if the compiled library is missing -- there is no CPU fallback.
 """
 import ctypes
 import os
@@ -85,7 +85,19 @@ def _load():
     return L
 
 
-lib = _load()
+class _Lib:
+    """libpic, loaded on first use (so that the build module can be imported before it exists);
+    a missing library raises ImportError at that point -- there is no fallback."""
+
+    _L = None
+
+    def __getattr__(self, name):
+        if _Lib._L is None:
+            _Lib._L = _load()
+        return getattr(_Lib._L, name)
+
+
+lib = _Lib()
 
 
 def _check(st, h=None):
