@@ -159,12 +159,62 @@ __device__ __forceinline__ void boris(float eps, const float* eb, float* u) {
     u[2] = ul2 + eps * eb[2];
 }
 
-__device__ __forceinline__ void advance_axis(int& i, float& o, float d) {
-    float t = o + d;
+// Error-free transforms (Knuth TwoSum, FMA TwoProd) for float-float arithmetic.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = a * b;
+    e = fmaf(a, b, -p);
+}
+
+// gamma = sqrt(1 + |u|^2) as an unevaluated float-float sum gh + gl.
+__device__ __forceinline__ void gamma_ff(const float* u, float& gh, float& gl) {
+    float sh = 1.f, sl = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float ph, pl, t, e;
+        two_prod(u[d], u[d], ph, pl);
+        two_sum(sh, ph, t, e);
+        sh = t;
+        sl += e + pl;
+    }
+    float t = sh + sl;
+    sl = sl - (t - sh);
+    sh = t;
+    gh = sqrtf(sh);
+    gl = (fmaf(-gh, gh, sh) + sl) * (0.5f / gh);
+}
+
+// Displacement u_a dt / (gamma h_a) in cells as dh + dl (k = dt/h_a given as kh + kl).  Computed
+// to ~1e-13 relative so that the per-step FP32 rounding of the offset is the only error left:
+// rounding to nearest of o + (dh + dl) is unbiased, while a once-rounded FP32 increment would
+// drift by the same fraction of an ulp every step.
+__device__ __forceinline__ void displacement(float ua, float gh, float gl, float kh, float kl, float& dh,
+                                             float& dl) {
+    float qh = ua / gh;
+    float ql = (fmaf(-qh, gh, ua) - qh * gl) / gh;
+    dh = qh * kh;
+    dl = fmaf(qh, kh, -dh) + (qh * kl + ql * kh);
+}
+
+// o + (dh + dl) -> new cell and offset in [0, 1), with one rounding of the exact sum.
+__device__ __forceinline__ void advance_axis(int& i, float& o, float dh, float dl) {
+    float s, e;
+    two_sum(o, dh, s, e);
+    float t = s + (e + dl);
     float fl = floorf(t);
-    t -= fl;
+    float r, re;
+    two_sum(s, -fl, r, re);                   // exact: fl is an integer near s
+    t = r + (e + dl + re);
     int di = (int)fl;
-    if (t >= 1.f) {      // t was within round-off below an integer
+    if (t < 0.f) {                            // the rounded sum sat within round-off of fl
+        t += 1.f;
+        di -= 1;
+    }
+    if (t >= 1.f) {
         t -= 1.f;
         di += 1;
     }
@@ -347,21 +397,24 @@ __device__ __forceinline__ void push_one(const GridP& g, const SpeciesP& sp, con
     gather<NDIM, SHAPE>(g, E, B, p0, eb);
     boris(sp.eps, eb, u);
 
-    float gam = sqrtf(1.f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    float ig = 1.f / gam;
-    Pos p1 = p0;
-    float mz = u[0] * ig * (g.dt / g.dz), mx = u[1] * ig * (g.dt / g.dx);
-    float my = NDIM == 3 ? u[2] * ig * (g.dt / g.dy) : 0.f;
+    float gh, gl;
+    gamma_ff(u, gh, gl);
+    float dzh, dzl, dxh, dxl, dyh = 0.f, dyl = 0.f;
+    displacement(u[0], gh, gl, sp.kz[0], sp.kz[1], dzh, dzl);
+    displacement(u[1], gh, gl, sp.kx[0], sp.kx[1], dxh, dxl);
+    if (NDIM == 3) displacement(u[2], gh, gl, sp.ky[0], sp.ky[1], dyh, dyl);
     // |v| < c and dt below the stability limit keep every move under one cell; anything else
     // (a non-finite field or momentum) retires the particle instead of indexing outside.
-    if (!(fabsf(mz) < 1.f && fabsf(mx) < 1.f && fabsf(my) < 1.f)) {
+    if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f && fabsf(dyh) < 1.f)) {
         sp.cell[p] = -1;
         if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
         return;
     }
-    advance_axis(p1.iz, p1.oz, mz);
-    advance_axis(p1.ix, p1.ox, mx);
-    if (NDIM == 3) advance_axis(p1.iy, p1.oy, my);
+    Pos p1 = p0;
+    advance_axis(p1.iz, p1.oz, dzh, dzl);
+    advance_axis(p1.ix, p1.ox, dxh, dxl);
+    if (NDIM == 3) advance_axis(p1.iy, p1.oy, dyh, dyl);
+    const float ig = 1.f / gh;
 
     if (MODE == MODE_FUSED) deposit<NDIM, SHAPE>(g, sp.qv, u[2] * ig, p0, p1, J);
 

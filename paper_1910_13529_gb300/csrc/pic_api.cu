@@ -142,6 +142,12 @@ SpeciesP species_params(pic_t* h, int s) {
     p.cap = q.cap;
     double V = h->cfg.dz * h->cfg.dx * (h->cfg.ndim == 3 ? h->cfg.dy : 1.0);
     p.eps = (float)(q.q * h->cfg.dt / (2.0 * q.m));
+    const double k3[3] = {h->cfg.dt / h->cfg.dz, h->cfg.dt / h->cfg.dx, h->cfg.dt / h->cfg.dy};
+    float* dst[3] = {p.kz, p.kx, p.ky};
+    for (int a = 0; a < 3; ++a) {
+        dst[a][0] = (float)k3[a];
+        dst[a][1] = (float)(k3[a] - (double)dst[a][0]);
+    }
     p.qv64 = q.q * q.w / V;
     p.qv = (float)p.qv64;
     p.wm = q.w * q.m;

@@ -47,6 +47,7 @@ struct SpeciesP {
     int32_t* count;      // device live-slot extent
     long long cap;
     float eps;           // q dt / (2 m)   (Boris)
+    float kz[2], kx[2], ky[2];   // dt/dz, dt/dx, dt/dy as float-float (hi, lo)
     float qv;            // q w / V        (charge density of one macro-particle per unit shape)
     double qv64;
     double wm;           // w m            (kinetic energy)

@@ -61,7 +61,7 @@ class Simulation:
 
     def add_species(self, s, iz, ix, iy, off, u, q, m, w, cap=None, ids=None):
         n = len(iz)
-        cap = int(cap if cap is not None else max(n, 1))
+        cap = max(int(cap if cap is not None else n), 1)
         cell = torch.full((cap,), -1, dtype=torch.int32, device=self.device)
         offt = torch.zeros((self.ndim, cap), dtype=torch.float32, device=self.device)
         ut = torch.zeros((3, cap), dtype=torch.float32, device=self.device)
