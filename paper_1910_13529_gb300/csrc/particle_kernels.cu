@@ -10,6 +10,7 @@
 // round-off per step with no drift from re-rounded positions.
 #include <cuda_runtime.h>
 
+#include <climits>
 #include <type_traits>
 
 #include "pic_internal.h"
@@ -223,144 +224,129 @@ __device__ __forceinline__ void advance_axis(int& i, float& o, float dh, float d
 }
 
 // ---------------------------------------------------------------- deposit ----
+// Current accumulators: add(component, node z, node x, node y, value) with x, y not yet wrapped.
+struct GlobalAcc {
+    const GridP* g;
+    float* J;
+    __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
+        if (gz < 0 || gz >= g->nz) return;
+        long long o = ((long long)wrapi(gy, g->ny) * g->nx + wrapi(gx, g->nx)) * g->nz + gz;
+        atomicAdd(J + c * g->ncell + o, v);
+    }
+};
+// A box of nodes [z0, z0+zl) x [x0, x0+xl) x [y0, y0+yl) in shared memory, 3 components.
+struct SharedAcc {
+    float* s;
+    int z0, x0, y0, zl, xl, vol;
+    __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
+        atomicAdd(s + c * vol + ((gy - y0) * xl + (gx - x0)) * zl + (gz - z0), v);
+    }
+};
+
+// first node of the deposition window of a move (the lower of the two shape supports)
+template <int SHAPE>
+__device__ __forceinline__ int window_base(int i0, float o0, int i1, float o1) {
+    float w[Shape<SHAPE>::K];
+    int b0 = i0 + Shape<SHAPE>::w(o0, w);
+    int b1 = i1 + Shape<SHAPE>::w(o1, w);
+    return min(b0, b1);
+}
+
+template <int SHAPE>
+__device__ __forceinline__ int axis_weights(int i0, float o0, int i1, float o1, float* S0, float* DS) {
+    constexpr int K = Shape<SHAPE>::K;
+    constexpr int KW = K + 1;
+    float w0[K], w1[K];
+    int b0 = i0 + Shape<SHAPE>::w(o0, w0);
+    int b1 = i1 + Shape<SHAPE>::w(o1, w1);
+    int b = min(b0, b1);
+    int s0 = b0 - b, s1 = b1 - b;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
+        float c = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
+        S0[k] = a;
+        DS[k] = c - a;
+    }
+    return b;
+}
+
 // Esirkepov current of one particle moving p0 -> p1 (|displacement| < 1 cell per axis).
 // 2D: W1 = dSz (S0x + dSx/2), W2 = dSx (S0z + dSz/2), W3 = S0z S0x + dSz S0x/2 + S0z dSx/2 + dSz dSx/3.
 // 3D: W_a = dS_a (S0_b S0_c + dS_b S0_c/2 + S0_b dS_c/2 + dS_b dS_c/3).
 // J_a = -(q w/V)(h_a/dt) cumsum_a W_a; 2D J3 = (q w/V) v3 W3.
-template <int NDIM, int SHAPE>
-__device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, const Pos& p0,
-                                        const Pos& p1, float* __restrict__ J) {
-    constexpr int K = Shape<SHAPE>::K;
-    constexpr int KW = K + 1;
-    float w0[K], w1[K];
+template <int NDIM, int SHAPE, typename Acc>
+__device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, const Pos& p0, const Pos& p1,
+                                        const Acc& acc) {
+    constexpr int KW = Shape<SHAPE>::K + 1;
     float S0z[KW], DSz[KW], S0x[KW], DSx[KW], S0y[KW], DSy[KW];
-    int bz, bx, by = 0;
-    {
-        int b0 = p0.iz + Shape<SHAPE>::w(p0.oz, w0);
-        int b1 = p1.iz + Shape<SHAPE>::w(p1.oz, w1);
-        bz = min(b0, b1);
-        int s0 = b0 - bz, s1 = b1 - bz;
-#pragma unroll
-        for (int k = 0; k < KW; ++k) {
-            float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
-            float b = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
-            S0z[k] = a;
-            DSz[k] = b - a;
-        }
-    }
-    {
-        int b0 = p0.ix + Shape<SHAPE>::w(p0.ox, w0);
-        int b1 = p1.ix + Shape<SHAPE>::w(p1.ox, w1);
-        bx = min(b0, b1);
-        int s0 = b0 - bx, s1 = b1 - bx;
-#pragma unroll
-        for (int k = 0; k < KW; ++k) {
-            float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
-            float b = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
-            S0x[k] = a;
-            DSx[k] = b - a;
-        }
-    }
-    if (NDIM == 3) {
-        int b0 = p0.iy + Shape<SHAPE>::w(p0.oy, w0);
-        int b1 = p1.iy + Shape<SHAPE>::w(p1.oy, w1);
-        by = min(b0, b1);
-        int s0 = b0 - by, s1 = b1 - by;
-#pragma unroll
-        for (int k = 0; k < KW; ++k) {
-            float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
-            float b = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
-            S0y[k] = a;
-            DSy[k] = b - a;
-        }
-    }
-    const long long N = g.ncell;
+    const int bz = axis_weights<SHAPE>(p0.iz, p0.oz, p1.iz, p1.oz, S0z, DSz);
+    const int bx = axis_weights<SHAPE>(p0.ix, p0.ox, p1.ix, p1.ox, S0x, DSx);
+    const int by = NDIM == 3 ? axis_weights<SHAPE>(p0.iy, p0.oy, p1.iy, p1.oy, S0y, DSy) : 0;
     const float f1 = -qv * g.dz / g.dt, f2 = -qv * g.dx / g.dt;
-    int gxs[KW];
-#pragma unroll
-    for (int k = 0; k < KW; ++k) gxs[k] = wrapi(bx + k, g.nx);
-
     if (NDIM == 2) {
-        // J1: cumulative along z for each x row
 #pragma unroll
-        for (int b = 0; b < KW; ++b) {
+        for (int b = 0; b < KW; ++b) {           // J1: cumulative along z
             float tx = S0x[b] + 0.5f * DSx[b];
-            long long row = (long long)gxs[b] * g.nz;
             float cum = 0.f;
 #pragma unroll
             for (int a = 0; a < KW - 1; ++a) {
                 cum += DSz[a] * tx;
-                int gz = bz + a;
-                if (gz >= 0 && gz < g.nz && cum != 0.f) atomicAdd(J + row + gz, f1 * cum);
+                if (cum != 0.f) acc.add(0, bz + a, bx + b, 0, f1 * cum);
             }
         }
-        // J2: cumulative along x for each z column; J3
 #pragma unroll
-        for (int a = 0; a < KW; ++a) {
-            int gz = bz + a;
-            if (gz < 0 || gz >= g.nz) continue;
+        for (int a = 0; a < KW; ++a) {           // J2: cumulative along x; J3
             float tz = S0z[a] + 0.5f * DSz[a];
             float cum = 0.f;
 #pragma unroll
             for (int b = 0; b < KW; ++b) {
-                long long o = (long long)gxs[b] * g.nz + gz;
                 if (b < KW - 1) {
                     cum += DSx[b] * tz;
-                    if (cum != 0.f) atomicAdd(J + N + o, f2 * cum);
+                    if (cum != 0.f) acc.add(1, bz + a, bx + b, 0, f2 * cum);
                 }
                 float w3 = S0z[a] * S0x[b] + 0.5f * DSz[a] * S0x[b] + 0.5f * S0z[a] * DSx[b]
                          + (1.f / 3.f) * DSz[a] * DSx[b];
-                if (w3 != 0.f) atomicAdd(J + 2 * N + o, qv * v3 * w3);
+                if (w3 != 0.f) acc.add(2, bz + a, bx + b, 0, qv * v3 * w3);
             }
         }
     } else {
         const float f3 = -qv * g.dy / g.dt;
-        int gys[KW];
-#pragma unroll
-        for (int k = 0; k < KW; ++k) gys[k] = wrapi(by + k, g.ny);
-        // J1 along z
 #pragma unroll
         for (int c = 0; c < KW; ++c)
 #pragma unroll
-            for (int b = 0; b < KW; ++b) {
+            for (int b = 0; b < KW; ++b) {       // J1 along z
                 float t = S0x[b] * S0y[c] + 0.5f * DSx[b] * S0y[c] + 0.5f * S0x[b] * DSy[c]
                         + (1.f / 3.f) * DSx[b] * DSy[c];
-                long long row = ((long long)gys[c] * g.nx + gxs[b]) * g.nz;
                 float cum = 0.f;
 #pragma unroll
                 for (int a = 0; a < KW - 1; ++a) {
                     cum += DSz[a] * t;
-                    int gz = bz + a;
-                    if (gz >= 0 && gz < g.nz && cum != 0.f) atomicAdd(J + row + gz, f1 * cum);
+                    if (cum != 0.f) acc.add(0, bz + a, bx + b, by + c, f1 * cum);
                 }
             }
-        // J2 along x, J3 along y
 #pragma unroll
         for (int a = 0; a < KW; ++a) {
-            int gz = bz + a;
-            if (gz < 0 || gz >= g.nz) continue;
 #pragma unroll
-            for (int c = 0; c < KW; ++c) {
+            for (int c = 0; c < KW; ++c) {       // J2 along x
                 float t = S0z[a] * S0y[c] + 0.5f * DSz[a] * S0y[c] + 0.5f * S0z[a] * DSy[c]
                         + (1.f / 3.f) * DSz[a] * DSy[c];
                 float cum = 0.f;
 #pragma unroll
                 for (int b = 0; b < KW - 1; ++b) {
                     cum += DSx[b] * t;
-                    long long o = ((long long)gys[c] * g.nx + gxs[b]) * g.nz + gz;
-                    if (cum != 0.f) atomicAdd(J + N + o, f2 * cum);
+                    if (cum != 0.f) acc.add(1, bz + a, bx + b, by + c, f2 * cum);
                 }
             }
 #pragma unroll
-            for (int b = 0; b < KW; ++b) {
+            for (int b = 0; b < KW; ++b) {       // J3 along y
                 float t = S0z[a] * S0x[b] + 0.5f * DSz[a] * S0x[b] + 0.5f * S0z[a] * DSx[b]
                         + (1.f / 3.f) * DSz[a] * DSx[b];
                 float cum = 0.f;
 #pragma unroll
                 for (int c = 0; c < KW - 1; ++c) {
                     cum += DSy[c] * t;
-                    long long o = ((long long)gys[c] * g.nx + gxs[b]) * g.nz + gz;
-                    if (cum != 0.f) atomicAdd(J + 2 * N + o, f3 * cum);
+                    if (cum != 0.f) acc.add(2, bz + a, bx + b, by + c, f3 * cum);
                 }
             }
         }
@@ -370,23 +356,24 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 // ---------------------------------------------------------------- kernels ----
 enum { MODE_FUSED = 0, MODE_PUSH_ONLY = 1 };
 
+// Gather, Boris, move one particle and store its new state.  Returns false for an empty,
+// retired or out-of-window slot.  p0/p1: old and new positions (p1.ix, p1.iy unwrapped).
 template <int NDIM, int SHAPE, int MODE>
-__device__ __forceinline__ void push_one(const GridP& g, const SpeciesP& sp, const float* __restrict__ E,
-                                         const float* __restrict__ B, float* __restrict__ J, int shift,
-                                         long long p, long long cap) {
+__device__ __forceinline__ bool advance_one(const GridP& g, const SpeciesP& sp, const float* __restrict__ E,
+                                            const float* __restrict__ B, int shift, long long p, long long cap,
+                                            Pos& p0, Pos& p1, float& v3) {
     int cell = sp.cell[p];
     if (cell < 0) {
         if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
-        return;
+        return false;
     }
-    Pos p0;
     int izg;
     decode(g, cell, izg, p0.ix, p0.iy);
     p0.iz = izg - 1 - shift;
     if (p0.iz < 0 || p0.iz >= g.nz) {      // left through the back of the window (or stale)
         sp.cell[p] = -1;
         if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
-        return;
+        return false;
     }
     p0.oz = sp.off[p];
     p0.ox = sp.off[cap + p];
@@ -408,15 +395,13 @@ __device__ __forceinline__ void push_one(const GridP& g, const SpeciesP& sp, con
     if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f && fabsf(dyh) < 1.f)) {
         sp.cell[p] = -1;
         if (MODE == MODE_PUSH_ONLY) sp.prev_cell[p] = -1;
-        return;
+        return false;
     }
-    Pos p1 = p0;
+    p1 = p0;
     advance_axis(p1.iz, p1.oz, dzh, dzl);
     advance_axis(p1.ix, p1.ox, dxh, dxl);
     if (NDIM == 3) advance_axis(p1.iy, p1.oy, dyh, dyl);
-    const float ig = 1.f / gh;
-
-    if (MODE == MODE_FUSED) deposit<NDIM, SHAPE>(g, sp.qv, u[2] * ig, p0, p1, J);
+    v3 = u[2] / gh;
 
     int wx = wrapi(p1.ix, g.nx);
     int wy = NDIM == 3 ? wrapi(p1.iy, g.ny) : 0;
@@ -435,19 +420,101 @@ __device__ __forceinline__ void push_one(const GridP& g, const SpeciesP& sp, con
     sp.u[p] = u[0];
     sp.u[cap + p] = u[1];
     sp.u[2 * cap + p] = u[2];
+    return true;
 }
 
-
-template <int NDIM, int SHAPE, int MODE>
+// Gather + push only; the old positions are kept for pic_deposit.
+template <int NDIM, int SHAPE>
 __global__ void __launch_bounds__(256) push_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
-                                                   const float* __restrict__ B, float* __restrict__ J,
-                                                   int shift) {
+                                                   const float* __restrict__ B, int shift) {
     const long long n = *sp.count;
     const long long cap = sp.cap;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x)
-        push_one<NDIM, SHAPE, MODE>(g, sp, E, B, J, shift, p, cap);
+         p += (long long)gridDim.x * blockDim.x) {
+        Pos p0, p1;
+        float v3;
+        advance_one<NDIM, SHAPE, MODE_PUSH_ONLY>(g, sp, E, B, shift, p, cap, p0, p1, v3);
+    }
 }
+
+// Shared-memory current box of the fused kernel: 3 components, at most BOX_CAP floats.
+constexpr int FUSED_T = 256;
+constexpr int BOX_CAP = 12288;
+
+// Gather + Boris + move + Esirkepov deposition, fused.  Each CTA takes chunks of FUSED_T
+// consecutive particles (cell-sorted, so a chunk covers a compact patch of cells); the chunk's
+// currents are accumulated in a shared-memory box spanning its deposition windows and then
+// added to J once per non-zero node.  A chunk whose box exceeds BOX_CAP (unsorted particles,
+// a chunk across the periodic seam) deposits straight to global memory.
+template <int NDIM, int SHAPE>
+__global__ void __launch_bounds__(FUSED_T) push_deposit_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
+                                                               const float* __restrict__ B, float* __restrict__ J,
+                                                               int shift) {
+    extern __shared__ float sJ[];
+    __shared__ int box[6];
+    constexpr int KW = Shape<SHAPE>::K + 1;
+    const long long n = *sp.count;
+    const long long cap = sp.cap;
+    const int lane = threadIdx.x & 31;
+    for (long long base = (long long)blockIdx.x * FUSED_T; base < n; base += (long long)gridDim.x * FUSED_T) {
+        if (threadIdx.x < 6) box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        __syncthreads();
+        const long long p = base + threadIdx.x;
+        Pos p0, p1;
+        float v3 = 0.f;
+        bool ok = p < n && advance_one<NDIM, SHAPE, MODE_FUSED>(g, sp, E, B, shift, p, cap, p0, p1, v3);
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        if (ok) {
+            lo[0] = window_base<SHAPE>(p0.iz, p0.oz, p1.iz, p1.oz);
+            lo[1] = window_base<SHAPE>(p0.ix, p0.ox, p1.ix, p1.ox);
+            lo[2] = NDIM == 3 ? window_base<SHAPE>(p0.iy, p0.oy, p1.iy, p1.oy) : 0;
+            hi[0] = lo[0] + KW - 1;
+            hi[1] = lo[1] + KW - 1;
+            hi[2] = NDIM == 3 ? lo[2] + KW - 1 : 0;
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            int mn = __reduce_min_sync(0xffffffffu, lo[a]);
+            int mx = __reduce_max_sync(0xffffffffu, hi[a]);
+            if (lane == 0 && mn != INT_MAX) {
+                atomicMin(&box[2 * a], mn);
+                atomicMax(&box[2 * a + 1], mx);
+            }
+        }
+        __syncthreads();
+        const bool any = box[0] != INT_MAX;
+        const int zl = any ? box[1] - box[0] + 1 : 0;
+        const int xl = any ? box[3] - box[2] + 1 : 0;
+        const int yl = any ? box[5] - box[4] + 1 : 0;
+        const long long vol = (long long)zl * xl * yl;
+        if (any && 3 * vol <= BOX_CAP) {
+            const int v = (int)vol;
+            for (int i = threadIdx.x; i < 3 * v; i += FUSED_T) sJ[i] = 0.f;
+            __syncthreads();
+            if (ok) {
+                SharedAcc acc{sJ, box[0], box[2], box[4], zl, xl, v};
+                deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, acc);
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < 3 * v; i += FUSED_T) {
+                float val = sJ[i];
+                if (val == 0.f) continue;
+                int c = i / v, r = i - c * v;
+                int z = r % zl, q = r / zl;
+                int x = q % xl, y = q / xl;
+                int gz = box[0] + z;
+                if (gz < 0 || gz >= g.nz) continue;
+                long long o = ((long long)wrapi(box[4] + y, g.ny) * g.nx + wrapi(box[2] + x, g.nx)) * g.nz + gz;
+                atomicAdd(J + c * g.ncell + o, val);
+            }
+        } else if (ok) {
+            GlobalAcc acc{&g, J};
+            deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, acc);
+        }
+        __syncthreads();
+    }
+}
+
 template <int NDIM, int SHAPE>
 __device__ __forceinline__ void deposit_one(const GridP& g, const SpeciesP& sp, float* __restrict__ J,
                                             long long p) {
@@ -473,9 +540,11 @@ __device__ __forceinline__ void deposit_one(const GridP& g, const SpeciesP& sp, 
     p1.oz = sp.off[p];
     p1.ox = sp.off[cap + p];
     p1.oy = NDIM == 3 ? sp.off[2 * cap + p] : 0.f;
-    float u0 = sp.u[p], u1 = sp.u[cap + p], u2 = sp.u[2 * cap + p];
-    float ig = 1.f / sqrtf(1.f + u0 * u0 + u1 * u1 + u2 * u2);
-    deposit<NDIM, SHAPE>(g, sp.qv, u2 * ig, p0, p1, J);
+    float u[3] = {sp.u[p], sp.u[cap + p], sp.u[2 * cap + p]};
+    float gh, gl;
+    gamma_ff(u, gh, gl);
+    GlobalAcc acc{&g, J};
+    deposit<NDIM, SHAPE>(g, sp.qv, u[2] / gh, p0, p1, acc);
     if (p1.iz < 0 || p1.iz >= g.nz) sp.cell[p] = -1;
 }
 
@@ -698,10 +767,19 @@ cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, cons
     if (extent <= 0) return cudaSuccess;
     return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
         constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
-        if (mode == MODE_FUSED)
-            push_kernel<ND, SH, MODE_FUSED><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, J, shift);
-        else
-            push_kernel<ND, SH, MODE_PUSH_ONLY><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, J, shift);
+        if (mode == MODE_FUSED) {
+            auto k = push_deposit_kernel<ND, SH>;
+            static bool configured = false;
+            if (!configured) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)(BOX_CAP * sizeof(float)));
+                if (e != cudaSuccess) return e;
+                configured = true;
+            }
+            k<<<pblocks(extent), FUSED_T, BOX_CAP * sizeof(float), s>>>(g, sp, E, B, J, shift);
+        } else {
+            push_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, shift);
+        }
         return cudaGetLastError();
     });
 }

@@ -104,11 +104,13 @@ def gaussian_beam(ndim, nz, nx, ny, d, n, sigma_z, sigma_r, gamma, spread, peak_
     x = nx * d[1] / 2 + tnorm(n, sigma_r)
     cz, oz = _split(z / d[0])
     cx, ox = _split(x / d[1])
+    cx = np.mod(cx, nx)                      # periodic transverse axes
     offs = [oz, ox]
     cy = np.zeros(n, np.int64)
     if dims == 3:
         y = ny * d[2] / 2 + tnorm(n, sigma_r)
         cy, oy = _split(y / d[2])
+        cy = np.mod(cy, ny)
         offs.append(oy)
     g = gamma * (1.0 + spread * (rng.uniform(size=n) - 0.5))
     u = np.zeros((3, n), np.float32)

@@ -226,11 +226,11 @@ def test_moving_window_beam_plasma():
         osim.step()
     step, shifts, pend = sim.state()
     assert shifts == osim.shifts and shifts >= 10
-    assert field_error(sim, osim) < 1e-4
-    assert field_rel_l2(sim, osim) < 1e-4
+    assert field_error(sim, osim) < TOL
+    assert field_rel_l2(sim, osim) < TOL
     for s in range(2):
         dx, du = particle_errors(sim, osim, s, 2, pending_shift=pend)
-        assert dx < 1e-4 and du < 1e-4, (s, dx, du)
+        assert dx < TOL and du < TOL, (s, dx, du)
     sim.close()
 
 

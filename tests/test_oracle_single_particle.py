@@ -1,0 +1,39 @@
+"""The oracle's field of one free-streaming relativistic particle against the paper's k-space
+integral for E1 (Sec. 2.2, Eq. E12D with the Appendix D k2 integral), evaluated by quadrature.
+
+Yee solver, dx1 = dx2 = 1 (r = 1), kappa = dx1/dt = 4, linear shape, beta -> 1 (gamma = 1e7),
+moving window at c so the particle stays in the box; compared after 2000 steps (the particle
+has crossed 500 cells), at a step where it sits on a node (N integer).  The integral keeps the
+nu1 = 0 and nu1 = +-1 zones; Sec. 2.2 notes that the neglected higher zones matter next to the
+particle, so |i'| <= 1 is excluded and the band is 10% of the largest |E1|."""
+import math
+import warnings
+
+import numpy as np
+
+from oracle import core as oc
+from oracle import kspace
+
+warnings.filterwarnings("ignore")
+
+
+def test_yee_on_axis_e1_matches_kspace_integral():
+    nz, nx = 256, 128
+    g = oc.Grid(2, nz, nx, 1, 1.0, 1.0, 1.0, 0.25, C=(1.0,), shape=1)
+    gam = 1e7
+    xi = np.array([[nz - 40.0, nx // 2, 0.0]])
+    u = np.array([[math.sqrt(gam * gam - 1.0), 0.0, 0.0]])
+    sim = oc.Sim(g, [oc.Species(xi, u, 1.0, 1.0, 1.0)], moving_window=True)
+    for _ in range(2000):
+        sim.step()
+    p = sim.species[0].xi[0]
+    N, j0 = int(round(p[0])), int(round(p[1]))
+    assert abs(p[0] - N) < 1e-6            # on a node: N = n dt / dx1 is an integer
+    E1 = sim.E[0, 0, j0, :]
+    ips = [i for i in range(-12, 13) if abs(i) >= 2]
+    ref = np.array([kspace.e1_axis_yee(i, 4.0, 1.0, 1) for i in ips])
+    sim_v = np.array([E1[N + i] for i in ips])
+    band = 0.1 * np.max(np.abs(ref))
+    assert np.max(np.abs(sim_v - ref)) < band
+    # the Cerenkov wake lies behind the particle (Sec. 2.2)
+    assert np.max(np.abs(E1[N - 40:N - 10])) > 20 * np.max(np.abs(E1[N + 10:N + 30]))
