@@ -165,6 +165,28 @@ pic_status pic_diag(pic_t* h, double* out, void* stream);
 pic_status pic_rho(pic_t* h, double* rho, void* stream);
 /* G = d-.E - rho - rho_bg at every node (FP64, device). */
 pic_status pic_gauss(pic_t* h, double* G, void* stream);
+/* ---- Gauss residual without allocating ----------------------------------------------
+ * The paper has no counterpart to this entry point; it is a convenience of this library.
+ * pic_gauss needs an FP64 charge-density buffer of nz*nx*ny doubles, which the handle
+ * allocates with cudaMalloc.  Some callers cannot allocate at the moment they want the
+ * diagnostic: programs that pre-allocate a fixed device-memory budget at start-up and forbid
+ * later growth, and time-critical loops that must not call cudaMalloc because it can block
+ * until the whole device is idle.  pic_gauss_static computes exactly what pic_gauss computes
+ * (G = d-.E - rho - rho_bg, FP64, written to the caller's device array G of nz*nx*ny
+ * doubles) but takes its charge-density scratch from one array of PIC_STATIC_RHO_CELLS
+ * doubles (8 MiB) compiled into the library; every GPU that loads the library holds that
+ * array until the process exits.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call.
+ *   - Grids with more than PIC_STATIC_RHO_CELLS nodes are refused with PIC_ERR_ARG.
+ *   - The handle's device must be current.  The first call on a device looks up the array's
+ *     device address (cudaGetSymbolAddress) with that device current; later calls reuse it.
+ *   - All calls share the single array.  It is cleared at the start of every call, so
+ *     results never depend on an earlier call, but two calls that run at the same time on
+ *     the GPU (different streams or handles) race on it and give wrong results: order them
+ *     on one stream or synchronise between them.                                          */
+#define PIC_STATIC_RHO_CELLS (1 << 20)
+pic_status pic_gauss_static(pic_t* h, double* G, void* stream);
+
 /* Live-particle count of species s (synchronises stream). */
 pic_status pic_get_count(pic_t* h, int s, int64_t* n, void* stream);
 /* Completed steps, window shifts, and whether a shift is still pending on the particles. */

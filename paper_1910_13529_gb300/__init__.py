@@ -18,6 +18,7 @@ STATUS_NAMES = ["PIC_OK", "PIC_ERR_ARG", "PIC_ERR_CFL", "PIC_ERR_CUDA", "PIC_ERR
                 "PIC_ERR_STATE", "PIC_ERR_CAPACITY"]
 PIC_SOLVER_YEE, PIC_SOLVER_CUSTOM = 0, 1
 PIC_MAX_M, PIC_MAX_HLEN, PIC_MAX_SPECIES, PIC_DIAG_N = 16, 24, 4, 10
+PIC_STATIC_RHO_CELLS = 1 << 20
 DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "count", "step", "shifts",
              "status", "interior"]
 
@@ -25,7 +26,7 @@ DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "co
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_correction_taps",
            "pic_cfl_dt", "pic_get_coefficients", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
            "pic_deposit", "pic_field_advance", "pic_step", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
-           "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read"]
+           "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static"]
 TIMING_KEYS = ["particles", "deposit", "correction", "fields", "sort", "window", "diag"]
 
 
@@ -77,6 +78,7 @@ def _load():
         "pic_sync": ([vp, vp], ctypes.c_int),
         "pic_timing": ([vp, ctypes.c_int], ctypes.c_int),
         "pic_timing_read": ([vp, dp, i64p, vp], ctypes.c_int),
+        "pic_gauss_static": ([vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -194,6 +196,11 @@ def pic_rho(h, rho_ptr, stream):
 
 def pic_gauss(h, G_ptr, stream):
     _check(lib.pic_gauss(h, G_ptr, stream), h)
+
+
+def pic_gauss_static(h, G_ptr, stream):
+    """pic_gauss without allocating: scratch in a fixed in-library array (grids up to 2^20 nodes)."""
+    _check(lib.pic_gauss_static(h, G_ptr, stream), h)
 
 
 def pic_get_count(h, s, stream):

@@ -69,6 +69,13 @@ namespace {
 
 char g_create_err[256] = "no error";
 
+// Fixed FP64 charge-density scratch of pic_gauss_static (no allocation).  In host code the
+// name g_static_rho is only a stand-in: its device address is looked up per device with
+// cudaGetSymbolAddress (with that device current) and kept here.
+__device__ __align__(256) double g_static_rho[PIC_STATIC_RHO_CELLS];
+constexpr int kMaxDevices = 64;
+double* g_static_rho_addr[kMaxDevices] = {nullptr};
+
 pic_status fail(pic_t* h, pic_status st, const char* fmt, ...) {
     char* dst = h ? h->err : g_create_err;
     va_list ap;
@@ -560,6 +567,36 @@ pic_status pic_gauss(pic_t* h, double* G, void* stream) {
     if (st) return st;
     if ((st = pic_rho(h, h->rho64, stream))) return st;
     CK(h, launch_gauss(h->g, h->st, h->E, h->rho64, h->cfg.rho_bg, G, (cudaStream_t)stream), "gauss kernel");
+    return PIC_OK;
+}
+
+pic_status pic_gauss_static(pic_t* h, double* G, void* stream) {
+    if (!h || !G) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    if (h->g.ncell > PIC_STATIC_RHO_CELLS)
+        return fail(h, PIC_ERR_ARG, "pic_gauss_static: grid of %lld nodes exceeds the fixed scratch of %d nodes",
+                    h->g.ncell, PIC_STATIC_RHO_CELLS);
+    int dev = -1;
+    CK(h, cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != h->device)
+        return fail(h, PIC_ERR_ARG, "pic_gauss_static: device %d is current, the handle lives on device %d", dev,
+                    h->device);
+    if (dev < 0 || dev >= kMaxDevices) return fail(h, PIC_ERR_ARG, "pic_gauss_static: device index %d", dev);
+    if (!g_static_rho_addr[dev]) {
+        void* ptr = nullptr;
+        CK(h, cudaGetSymbolAddress(&ptr, g_static_rho), "cudaGetSymbolAddress of the fixed scratch");
+        g_static_rho_addr[dev] = static_cast<double*>(ptr);
+    }
+    double* rho = g_static_rho_addr[dev];
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(h, cudaMemsetAsync(rho, 0, sizeof(double) * h->g.ncell, s), "clear the fixed scratch");
+    for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
+        if (!h->sp[i].bound) continue;
+        SpeciesP sp = species_params(h, i);
+        CK(h, launch_rho(h->g, sp, h->pending_shift, rho, h->sp[i].extent, s), "rho kernel");
+    }
+    CK(h, launch_gauss(h->g, h->st, h->E, rho, h->cfg.rho_bg, G, s), "gauss kernel");
     return PIC_OK;
 }
 
