@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="reduced grid (profiling captures)")
+    ap.add_argument("--workload", default="beam2d", choices=["beam2d", "batch"],
+                    help="beam2d: the bench workload; batch: 256 independent single-particle runs, "
+                         "batched launch vs per-instance launches")
     return ap.parse_args()
 
 
@@ -311,8 +314,81 @@ def run_ours(args, rank, world, local_rank):
     sim.close()
 
 
+KAPPA_CFL_CUSTOM_2D = 1.632488686516034   # customised-stencil stability fixed point, r = 1
+
+
+def batch_configs(n=256, seed=4000):
+    """256 independent 2D single-particle vacuum runs: nz ~ U{128..1024}, nx ~ U{64..256},
+    log10 gamma ~ U[1, 5], dt = U[0.3, 0.99] x the instance's own solver limit, Yee or customised
+    (M = 16 fitted at the instance's kappa) by a fair coin, dz = dx = 0.05, linear shape."""
+    import math
+    rng = np.random.default_rng(seed)
+    d = 0.05
+    out = []
+    for i in range(n):
+        nz = int(rng.integers(128, 1025))
+        nx = int(rng.integers(64, 257))
+        gamma = 10 ** rng.uniform(1, 5)
+        frac = rng.uniform(0.3, 0.99)
+        custom = bool(rng.integers(0, 2))
+        dt = frac * (d / KAPPA_CFL_CUSTOM_2D if custom else d / math.sqrt(2))
+        cfg = dict(ndim=2, nz=nz, nx=nx, dz=d, dx=d, dt=dt, shape=1, solver="custom" if custom else "yee", M=16)
+        out.append((cfg, gamma))
+    return out
+
+
+def run_batch(args):
+    import torch
+    from paper_1910_13529_gb300 import workloads as wl
+    from paper_1910_13529_gb300.runtime import Batch, Simulation
+    dev = torch.device("cuda:0")
+    cfgs = batch_configs()
+    batch = Batch([c for c, _ in cfgs])
+    singles = []
+    cells = 0
+    for i, (c, gamma) in enumerate(cfgs):
+        _, sps = wl.single_particle(nz=c["nz"], nx=c["nx"], d=c["dz"], dt_over_dz=c["dt"] / c["dz"], gamma=gamma,
+                                    z_cell=c["nz"] / 8, x_cell=c["nx"] / 2)
+        sp = sps[0]
+        batch.instances[i].add_species(0, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"])
+        s1 = Simulation(device="cuda:0", **c)
+        s1.add_species(0, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"])
+        singles.append(s1)
+        cells += c["nz"] * c["nx"]
+    K = args.steps
+    batch.step(args.warmup)
+    for s1 in singles:
+        s1.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with ClockSampler(0) as clk:
+        e0.record()
+        batch.step(K)
+        e1.record()
+        for s1 in singles:
+            s1.step(K)
+        e2.record()
+        torch.cuda.synchronize(dev)
+    tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    value = cells * K / (tb / 1e3)
+    emit({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
+          "ms_per_step": tb / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+          "data": "synthetic (seeded instance parameters)",
+          "config": {"workload": "batched_vacuum_scan", "instances": len(cfgs), "cells_total": cells,
+                     "custom_instances": sum(1 for c, _ in cfgs if c["solver"] == "custom")},
+          "secondary": {"per_instance_launches_cell_updates_per_s": cells * K / (ts / 1e3),
+                        "speedup_batched_over_per_instance": ts / tb, "ms_batched": tb, "ms_per_instance": ts},
+          "clocks": clk.summary()})
+    for s1 in singles:
+        s1.close()
+    batch.close()
+
+
 def main():
     args = parse()
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

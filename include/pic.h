@@ -212,6 +212,30 @@ enum {
 pic_status pic_timing(pic_t* h, int enable);
 pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream);
 
+/* ---- tile autotuner ----------------------------------------------------------------------
+ * pic_autotune times each field-advance tile variant on the handle's bound fields (results go
+ * to library scratch; the state is unchanged; synchronises stream) and keeps the fastest for
+ * later steps.  The choice is cached per (ndim, stencil class, grid) for the process.
+ * pic_get_tuning: chosen variant, per-variant time in ms (0: not timed; ms needs 8 entries)
+ * and the number of variants (2D: 128x8, 256x4, 64x16, 256x8; 3D: 64x4x4, 128x4x2, 32x8x4).  */
+pic_status pic_autotune(pic_t* h, void* stream);
+pic_status pic_get_tuning(const pic_t* h, int* variant, double* ms, int* nvariants);
+
+/* ---- batched runs: many independent instances per launch --------------------------------
+ * A batch holds n independent 2D or 3D runs (no moving window, no sort), each with its own
+ * grid, dt, stencil (Yee or customised, own coefficients), shape and one particle species.
+ * pic_batch_step advances all of them with one launch per kernel class and step (J zero,
+ * gather/push/deposit, correction, field advance per stencil class), recorded once into a
+ * CUDA graph (two steps, one per field-buffer parity) and replayed on the caller's stream.
+ * Instance i is an ordinary handle (pic_batch_instance) for binding and diagnostics; bind its
+ * fields and species before the first pic_batch_step.  After pic_batch_step returns (on the
+ * stream) the bound field arrays of every instance hold the current fields.              */
+typedef struct pic_batch_t pic_batch_t;
+pic_status pic_batch_create(const pic_config* cfgs, int n, pic_batch_t** out);
+pic_status pic_batch_instance(pic_batch_t* b, int i, pic_t** h);
+pic_status pic_batch_step(pic_batch_t* b, int nsteps, void* stream);
+pic_status pic_batch_destroy(pic_batch_t* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -26,7 +26,9 @@ DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "co
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_correction_taps",
            "pic_cfl_dt", "pic_get_coefficients", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
            "pic_deposit", "pic_field_advance", "pic_step", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
-           "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static"]
+           "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
+           "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy",
+           "pic_autotune", "pic_get_tuning"]
 TIMING_KEYS = ["particles", "deposit", "correction", "fields", "sort", "window", "diag"]
 
 
@@ -79,6 +81,12 @@ def _load():
         "pic_timing": ([vp, ctypes.c_int], ctypes.c_int),
         "pic_timing_read": ([vp, dp, i64p, vp], ctypes.c_int),
         "pic_gauss_static": ([vp, vp, vp], ctypes.c_int),
+        "pic_batch_create": ([ctypes.POINTER(pic_config), ctypes.c_int, ctypes.POINTER(vp)], ctypes.c_int),
+        "pic_batch_instance": ([vp, ctypes.c_int, ctypes.POINTER(vp)], ctypes.c_int),
+        "pic_batch_step": ([vp, ctypes.c_int, vp], ctypes.c_int),
+        "pic_batch_destroy": ([vp], ctypes.c_int),
+        "pic_autotune": ([vp, vp], ctypes.c_int),
+        "pic_get_tuning": ([vp, ip, dp, ip], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -228,6 +236,38 @@ def pic_timing_read(h, stream):
     n = (ctypes.c_int64 * len(TIMING_KEYS))()
     _check(lib.pic_timing_read(h, _dptr(ms), n, stream), h)
     return dict(zip(TIMING_KEYS, ms.tolist())), dict(zip(TIMING_KEYS, list(n)))
+
+
+def pic_autotune(h, stream):
+    _check(lib.pic_autotune(h, stream), h)
+
+
+def pic_get_tuning(h):
+    v, nv = ctypes.c_int(), ctypes.c_int()
+    ms = np.zeros(8)
+    _check(lib.pic_get_tuning(h, ctypes.byref(v), _dptr(ms), ctypes.byref(nv)), h)
+    return v.value, ms[: nv.value]
+
+
+def pic_batch_create(cfgs):
+    arr = (pic_config * len(cfgs))(*cfgs)
+    b = ctypes.c_void_p()
+    _check(lib.pic_batch_create(arr, len(cfgs), ctypes.byref(b)))
+    return b
+
+
+def pic_batch_instance(b, i):
+    h = ctypes.c_void_p()
+    _check(lib.pic_batch_instance(b, int(i), ctypes.byref(h)))
+    return h
+
+
+def pic_batch_step(b, nsteps, stream):
+    _check(lib.pic_batch_step(b, int(nsteps), stream))
+
+
+def pic_batch_destroy(b):
+    _check(lib.pic_batch_destroy(b))
 
 
 def encode_cells(iz, ix, iy, nz, nx):

@@ -41,19 +41,19 @@ __device__ __forceinline__ int wrapi(int a, int n) {
     return a < 0 ? a + n : a;
 }
 
+// One output tile (tz, tx, ty) of the leapfrog field step, shared memory `smem`.
 template <int NDIM, int MAXM, int TZ, int TX, int TY>
-__global__ void __launch_bounds__(256) field_advance_kernel(FieldP p) {
+__device__ __forceinline__ void advance_tile(const FieldP& p, int tz, int tx, int ty, float* smem) {
     using T = Tile<NDIM, MAXM, TZ, TX, TY>;
-    extern __shared__ float smem[];
     float* sE = smem;                 // [3][RY0][RX0][W0]
     float* sB = smem + 3 * T::SE;     // [3][RY1][RX1][W1]
 
     const GridP& g = p.g;
     const int nz = g.nz, nx = g.nx, ny = g.ny;
     const long long N = g.ncell;
-    const int z0 = blockIdx.x * TZ;
-    const int x0 = blockIdx.y * TX;
-    const int y0 = NDIM == 3 ? blockIdx.z * TY : 0;
+    const int z0 = tz * TZ;
+    const int x0 = tx * TX;
+    const int y0 = NDIM == 3 ? ty * TY : 0;
     const int M = p.st.M;
 
     const float dt = g.dt;
@@ -220,6 +220,40 @@ __global__ void __launch_bounds__(256) field_advance_kernel(FieldP p) {
 }
 
 template <int NDIM, int MAXM, int TZ, int TX, int TY>
+__global__ void __launch_bounds__(256) field_advance_kernel(FieldP p) {
+    extern __shared__ float smem[];
+    advance_tile<NDIM, MAXM, TZ, TX, TY>(p, blockIdx.x, blockIdx.y, blockIdx.z, smem);
+}
+
+// Many independent grids in one launch: block b takes tile b of the concatenated tile list;
+// tile_start[i] is the first tile of instance i (tile_start[ninst] = total).  inst[2 i + parity]
+// holds instance i's parameters for this step's buffer direction.
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+__global__ void __launch_bounds__(256) field_advance_batch_kernel(const FieldP* __restrict__ inst,
+                                                                  const int* __restrict__ tile_start, int ninst,
+                                                                  int parity) {
+    extern __shared__ float smem[];
+    __shared__ FieldP sp;
+    __shared__ int sidx, slocal;
+    if (threadIdx.x == 0) {
+        const int t = blockIdx.x;
+        int lo = 0, hi = ninst - 1;          // last instance whose first tile is <= t
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        sidx = lo;
+        slocal = t - tile_start[lo];
+        sp = inst[2 * lo + parity];
+    }
+    __syncthreads();
+    const int ntz = (sp.g.nz + TZ - 1) / TZ, ntx = (sp.g.nx + TX - 1) / TX;
+    const int l = slocal;
+    const int tz = l % ntz, tx = (l / ntz) % ntx, ty = NDIM == 3 ? l / (ntz * ntx) : 0;
+    advance_tile<NDIM, MAXM, TZ, TX, TY>(sp, tz, tx, ty, smem);
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
 cudaError_t launch_fa(const FieldP& p, cudaStream_t s) {
     using T = Tile<NDIM, MAXM, TZ, TX, TY>;
     auto k = field_advance_kernel<NDIM, MAXM, TZ, TX, TY>;
@@ -262,20 +296,112 @@ __global__ void __launch_bounds__(256) correct_j1_kernel(CorrP p) {
     }
 }
 
+// Batched in-place correction: blockIdx.y = instance, blockIdx.x = z row of that instance.
+__global__ void __launch_bounds__(256) correct_j1_batch_kernel(const CorrInst* __restrict__ inst) {
+    extern __shared__ float s[];
+    const CorrInst& q = inst[blockIdx.y];
+    const int nz = q.g.nz, hl = q.hlen;
+    if ((long long)blockIdx.x >= (long long)q.g.nx * q.g.ny) return;
+    float* row = q.J1 + (long long)blockIdx.x * nz;
+    for (int i = threadIdx.x; i < nz + 2 * hl; i += blockDim.x) {
+        int gz = i - hl;
+        s[i] = (gz >= 0 && gz < nz) ? row[gz] : 0.f;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) {
+        float acc = 0.f;
+        for (int m = -hl; m <= hl; ++m) acc += q.h[m + hl] * s[i + hl - m];
+        row[i] = acc;
+    }
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+cudaError_t launch_fa_batch(const FieldP* inst, const int* tile_start, int ninst, int total, int parity,
+                            cudaStream_t s) {
+    using T = Tile<NDIM, MAXM, TZ, TX, TY>;
+    auto k = field_advance_batch_kernel<NDIM, MAXM, TZ, TX, TY>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<(unsigned)total, 256, T::smem_bytes, s>>>(inst, tile_start, ninst, parity);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s) {
+// Tiles of one grid in the batched field advance (same tile shapes as launch_field_advance_batch).
+int field_tiles(int ndim, int maxm, int nz, int nx, int ny) {
+    (void)maxm;
+    if (ndim == 2) return ((nz + 127) / 128) * ((nx + 7) / 8);
+    return ((nz + 63) / 64) * ((nx + 3) / 4) * ((ny + 3) / 4);
+}
+
+cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,
+                                       int ndim, int maxm, int parity, cudaStream_t s) {
+    if (ninst <= 0 || total_tiles <= 0) return cudaSuccess;
+    if (ndim == 2) {
+        if (maxm <= 1) return launch_fa_batch<2, 1, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+        if (maxm <= 4) return launch_fa_batch<2, 4, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+        if (maxm <= 8) return launch_fa_batch<2, 8, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+        return launch_fa_batch<2, 16, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+    }
+    if (maxm <= 1) return launch_fa_batch<3, 1, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+    if (maxm <= 4) return launch_fa_batch<3, 4, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+    if (maxm <= 8) return launch_fa_batch<3, 8, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+    return launch_fa_batch<3, 16, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+}
+
+cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_rows, int max_nz, cudaStream_t s) {
+    if (ninst <= 0) return cudaSuccess;
+    size_t smem = sizeof(float) * (max_nz + 2 * PIC_MAX_HLEN);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(correct_j1_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    correct_j1_batch_kernel<<<dim3((unsigned)max_rows, (unsigned)ninst), 256, smem, s>>>(inst);
+    return cudaGetLastError();
+}
+
+// Tile variants the autotuner chooses from.  2D: (TZ, TX); 3D: (TZ, TX, TY).
+//   2D: 0 = 128 x 8, 1 = 256 x 4, 2 = 64 x 16, 3 = 256 x 8
+//   3D: 0 = 64 x 4 x 4, 1 = 128 x 4 x 2, 2 = 32 x 8 x 4
+int field_variants(int ndim) { return ndim == 2 ? 4 : 3; }
+
+namespace {
+template <int NDIM, int MAXM>
+cudaError_t launch_fa_variant(const FieldP& p, int v, cudaStream_t s) {
+    if (NDIM == 2) {
+        switch (v) {
+            case 1: return launch_fa<2, MAXM, 256, 4, 1>(p, s);
+            case 2: return launch_fa<2, MAXM, 64, 16, 1>(p, s);
+            case 3: return launch_fa<2, MAXM, 256, 8, 1>(p, s);
+            default: return launch_fa<2, MAXM, 128, 8, 1>(p, s);
+        }
+    }
+    switch (v) {
+        case 1: return launch_fa<3, MAXM, 128, 4, 2>(p, s);
+        case 2: return launch_fa<3, MAXM, 32, 8, 4>(p, s);
+        default: return launch_fa<3, MAXM, 64, 4, 4>(p, s);
+    }
+}
+}  // namespace
+
+cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s, int variant) {
     const int M = p.st.M;
     if (p.g.ndim == 2) {
-        if (M <= 1) return launch_fa<2, 1, 128, 8, 1>(p, s);
-        if (M <= 4) return launch_fa<2, 4, 128, 8, 1>(p, s);
-        if (M <= 8) return launch_fa<2, 8, 128, 8, 1>(p, s);
-        return launch_fa<2, 16, 128, 8, 1>(p, s);
+        if (M <= 1) return launch_fa_variant<2, 1>(p, variant, s);
+        if (M <= 4) return launch_fa_variant<2, 4>(p, variant, s);
+        if (M <= 8) return launch_fa_variant<2, 8>(p, variant, s);
+        return launch_fa_variant<2, 16>(p, variant, s);
     }
-    if (M <= 1) return launch_fa<3, 1, 64, 4, 4>(p, s);
-    if (M <= 4) return launch_fa<3, 4, 64, 4, 4>(p, s);
-    if (M <= 8) return launch_fa<3, 8, 64, 4, 4>(p, s);
-    return launch_fa<3, 16, 64, 4, 4>(p, s);
+    if (M <= 1) return launch_fa_variant<3, 1>(p, variant, s);
+    if (M <= 4) return launch_fa_variant<3, 4>(p, variant, s);
+    if (M <= 8) return launch_fa_variant<3, 8>(p, variant, s);
+    return launch_fa_variant<3, 16>(p, variant, s);
 }
 
 cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s) {

@@ -57,9 +57,29 @@ __device__ __forceinline__ int half_weights(int cell, float o, float* W) {
     return cell - 1 + Shape<SHAPE>::w(o + 0.5f, W);
 }
 
-__device__ __forceinline__ int wrapi(int a, int n) {
-    a %= n;
-    return a < 0 ? a + n : a;
+// periodic wrap of an index at most one period outside [0, n)
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv& f) {
+    if (f.s < 0) return n;
+    uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> 1)) >> (f.s - 1);
+}
+
+// magic-number constants of the grid's divisors, computed on the device (batched instances)
+__device__ __forceinline__ FastDiv make_fastdiv_device(uint32_t d) {
+    FastDiv f{d, 0u, -1};
+    if (d <= 1) return f;
+    int l = 32 - __clz(d - 1);
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s = l;
+    return f;
+}
+
+__device__ __forceinline__ GridP prep_device(GridP g) {
+    g.div_nzg = make_fastdiv_device((uint32_t)g.nzg);
+    g.div_nx = make_fastdiv_device((uint32_t)g.nx);
+    return g;
 }
 
 struct Pos {
@@ -68,10 +88,11 @@ struct Pos {
 };
 
 __device__ __forceinline__ void decode(const GridP& g, int cell, int& izg, int& ix, int& iy) {
-    izg = cell % g.nzg;
-    int r = cell / g.nzg;
-    ix = r % g.nx;
-    iy = r / g.nx;
+    uint32_t r = fdiv((uint32_t)cell, g.div_nzg);
+    izg = cell - (int)r * g.nzg;
+    uint32_t q = fdiv(r, g.div_nx);
+    ix = (int)r - (int)q * g.nx;
+    iy = (int)q;
 }
 
 __device__ __forceinline__ int encode(const GridP& g, int iz, int ix, int iy) {
@@ -79,31 +100,39 @@ __device__ __forceinline__ int encode(const GridP& g, int iz, int ix, int iy) {
 }
 
 // ---------------------------------------------------------------- gather ----
+// sum_a,b(,c) Wz[a] Wx[b] (Wy[c]) F[row(b, c) + bz + a]; rows are precomputed z-row offsets
 template <int NDIM, int SHAPE>
-__device__ __forceinline__ float interp(const GridP& g, const float* __restrict__ F, int bz,
-                                        const float* Wz, int bx, const float* Wx, int by,
-                                        const float* Wy) {
+__device__ __forceinline__ float interp(const GridP& g, const float* __restrict__ F, int bz, const float* Wz,
+                                        const int* rows, const float* Wx, const float* Wy) {
     constexpr int K = Shape<SHAPE>::K;
     float acc = 0.f;
 #pragma unroll
     for (int c = 0; c < (NDIM == 3 ? K : 1); ++c) {
-        int gy = NDIM == 3 ? wrapi(by + c, g.ny) : 0;
         float wy = NDIM == 3 ? Wy[c] : 1.f;
 #pragma unroll
         for (int b = 0; b < K; ++b) {
-            int gx = wrapi(bx + b, g.nx);
-            long long row = ((long long)gy * g.nx + gx) * g.nz;
-            float wxy = wy * Wx[b];
+            const float* row = F + rows[c * K + b];
             float racc = 0.f;
 #pragma unroll
             for (int a = 0; a < K; ++a) {
                 int gz = bz + a;
-                if (gz >= 0 && gz < g.nz) racc += Wz[a] * __ldg(F + row + gz);
+                if ((unsigned)gz < (unsigned)g.nz) racc += Wz[a] * __ldg(row + gz);
             }
-            acc += wxy * racc;
+            acc += (wy * Wx[b]) * racc;
         }
     }
     return acc;
+}
+
+// z-row offsets of the K (x K) rows a stencil starting at (bx, by) touches
+template <int NDIM, int K>
+__device__ __forceinline__ void row_offsets(const GridP& g, int bx, int by, int* rows) {
+#pragma unroll
+    for (int c = 0; c < (NDIM == 3 ? K : 1); ++c) {
+        int yy = NDIM == 3 ? wrapi(by + c, g.ny) * g.nx : 0;
+#pragma unroll
+        for (int b = 0; b < K; ++b) rows[c * K + b] = (yy + wrapi(bx + b, g.nx)) * g.nz;
+    }
 }
 
 // E1..E3, B1..B3 at the particle (staggering: E1 z+, E2 x+, E3 y+ (3D) / node (2D),
@@ -112,6 +141,7 @@ template <int NDIM, int SHAPE>
 __device__ __forceinline__ void gather(const GridP& g, const float* __restrict__ E,
                                        const float* __restrict__ B, const Pos& p, float* eb) {
     constexpr int K = Shape<SHAPE>::K;
+    constexpr int R = NDIM == 3 ? K * K : K;
     float Wzn[K], Wzh[K], Wxn[K], Wxh[K], Wyn[K], Wyh[K];
     int bzn = p.iz + Shape<SHAPE>::w(p.oz, Wzn);
     int bzh = half_weights<SHAPE>(p.iz, p.oz, Wzh);
@@ -122,21 +152,24 @@ __device__ __forceinline__ void gather(const GridP& g, const float* __restrict__
         byn = p.iy + Shape<SHAPE>::w(p.oy, Wyn);
         byh = half_weights<SHAPE>(p.iy, p.oy, Wyh);
     }
-    const long long N = g.ncell;
+    const int N = (int)g.ncell;
+    int rnn[R], rhn[R];            // x node / x half rows, y node
+    row_offsets<NDIM, K>(g, bxn, byn, rnn);
+    row_offsets<NDIM, K>(g, bxh, byn, rhn);
+    eb[0] = interp<NDIM, SHAPE>(g, E, bzh, Wzh, rnn, Wxn, Wyn);
+    eb[1] = interp<NDIM, SHAPE>(g, E + N, bzn, Wzn, rhn, Wxh, Wyn);
+    eb[5] = interp<NDIM, SHAPE>(g, B + 2 * N, bzh, Wzh, rhn, Wxh, Wyn);
     if (NDIM == 3) {
-        eb[0] = interp<NDIM, SHAPE>(g, E, bzh, Wzh, bxn, Wxn, byn, Wyn);
-        eb[1] = interp<NDIM, SHAPE>(g, E + N, bzn, Wzn, bxh, Wxh, byn, Wyn);
-        eb[2] = interp<NDIM, SHAPE>(g, E + 2 * N, bzn, Wzn, bxn, Wxn, byh, Wyh);
-        eb[3] = interp<NDIM, SHAPE>(g, B, bzn, Wzn, bxh, Wxh, byh, Wyh);
-        eb[4] = interp<NDIM, SHAPE>(g, B + N, bzh, Wzh, bxn, Wxn, byh, Wyh);
-        eb[5] = interp<NDIM, SHAPE>(g, B + 2 * N, bzh, Wzh, bxh, Wxh, byn, Wyn);
+        int rnh[R], rhh[R];        // y half rows
+        row_offsets<NDIM, K>(g, bxn, byh, rnh);
+        row_offsets<NDIM, K>(g, bxh, byh, rhh);
+        eb[2] = interp<NDIM, SHAPE>(g, E + 2 * N, bzn, Wzn, rnh, Wxn, Wyh);
+        eb[3] = interp<NDIM, SHAPE>(g, B, bzn, Wzn, rhh, Wxh, Wyh);
+        eb[4] = interp<NDIM, SHAPE>(g, B + N, bzh, Wzh, rnh, Wxn, Wyh);
     } else {
-        eb[0] = interp<NDIM, SHAPE>(g, E, bzh, Wzh, bxn, Wxn, 0, nullptr);
-        eb[1] = interp<NDIM, SHAPE>(g, E + N, bzn, Wzn, bxh, Wxh, 0, nullptr);
-        eb[2] = interp<NDIM, SHAPE>(g, E + 2 * N, bzn, Wzn, bxn, Wxn, 0, nullptr);
-        eb[3] = interp<NDIM, SHAPE>(g, B, bzn, Wzn, bxh, Wxh, 0, nullptr);
-        eb[4] = interp<NDIM, SHAPE>(g, B + N, bzh, Wzh, bxn, Wxn, 0, nullptr);
-        eb[5] = interp<NDIM, SHAPE>(g, B + 2 * N, bzh, Wzh, bxh, Wxh, 0, nullptr);
+        eb[2] = interp<NDIM, SHAPE>(g, E + 2 * N, bzn, Wzn, rnn, Wxn, Wyn);
+        eb[3] = interp<NDIM, SHAPE>(g, B, bzn, Wzn, rhn, Wxh, Wyn);
+        eb[4] = interp<NDIM, SHAPE>(g, B + N, bzh, Wzh, rnn, Wxn, Wyn);
     }
 }
 
@@ -226,20 +259,36 @@ __device__ __forceinline__ void advance_axis(int& i, float& o, float dh, float d
 // ---------------------------------------------------------------- deposit ----
 // Current accumulators: add(component, node z, node x, node y, value) with x, y not yet wrapped.
 struct GlobalAcc {
+    static constexpr bool kAll = false;     // zero contributions are skipped
     const GridP* g;
     float* J;
     __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
         if (gz < 0 || gz >= g->nz) return;
-        long long o = ((long long)wrapi(gy, g->ny) * g->nx + wrapi(gx, g->nx)) * g->nz + gz;
-        atomicAdd(J + c * g->ncell + o, v);
+        int o = (wrapi(gy, g->ny) * g->nx + wrapi(gx, g->nx)) * g->nz + gz;
+        atomicAdd(J + c * (int)g->ncell + o, v);
     }
 };
 // A box of nodes [z0, z0+zl) x [x0, x0+xl) x [y0, y0+yl) in shared memory, 3 components.
 struct SharedAcc {
+    static constexpr bool kAll = false;
     float* s;
     int z0, x0, y0, zl, xl, vol;
     __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
         atomicAdd(s + c * vol + ((gy - y0) * xl + (gx - x0)) * zl + (gz - z0), v);
+    }
+};
+
+// All 32 lanes of a warp deposit into the same window: sum each contribution over the warp
+// and let lane 0 add it once (dense beams put many particles of a warp in one cell, and
+// their shared-memory atomics would otherwise serialise on the same addresses).
+struct WarpSharedAcc {
+    static constexpr bool kAll = true;      // every lane calls add() in lockstep
+    SharedAcc inner;
+    bool leader;
+    __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (leader && v != 0.f) inner.add(c, gz, gx, gy, v);
     }
 };
 
@@ -292,7 +341,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
             for (int a = 0; a < KW - 1; ++a) {
                 cum += DSz[a] * tx;
-                if (cum != 0.f) acc.add(0, bz + a, bx + b, 0, f1 * cum);
+                if (Acc::kAll || cum != 0.f) acc.add(0, bz + a, bx + b, 0, f1 * cum);
             }
         }
 #pragma unroll
@@ -303,11 +352,11 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
             for (int b = 0; b < KW; ++b) {
                 if (b < KW - 1) {
                     cum += DSx[b] * tz;
-                    if (cum != 0.f) acc.add(1, bz + a, bx + b, 0, f2 * cum);
+                    if (Acc::kAll || cum != 0.f) acc.add(1, bz + a, bx + b, 0, f2 * cum);
                 }
                 float w3 = S0z[a] * S0x[b] + 0.5f * DSz[a] * S0x[b] + 0.5f * S0z[a] * DSx[b]
                          + (1.f / 3.f) * DSz[a] * DSx[b];
-                if (w3 != 0.f) acc.add(2, bz + a, bx + b, 0, qv * v3 * w3);
+                if (Acc::kAll || w3 != 0.f) acc.add(2, bz + a, bx + b, 0, qv * v3 * w3);
             }
         }
     } else {
@@ -322,7 +371,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
                 for (int a = 0; a < KW - 1; ++a) {
                     cum += DSz[a] * t;
-                    if (cum != 0.f) acc.add(0, bz + a, bx + b, by + c, f1 * cum);
+                    if (Acc::kAll || cum != 0.f) acc.add(0, bz + a, bx + b, by + c, f1 * cum);
                 }
             }
 #pragma unroll
@@ -335,7 +384,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
                 for (int b = 0; b < KW - 1; ++b) {
                     cum += DSx[b] * t;
-                    if (cum != 0.f) acc.add(1, bz + a, bx + b, by + c, f2 * cum);
+                    if (Acc::kAll || cum != 0.f) acc.add(1, bz + a, bx + b, by + c, f2 * cum);
                 }
             }
 #pragma unroll
@@ -346,7 +395,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
                 for (int c = 0; c < KW - 1; ++c) {
                     cum += DSy[c] * t;
-                    if (cum != 0.f) acc.add(2, bz + a, bx + b, by + c, f3 * cum);
+                    if (Acc::kAll || cum != 0.f) acc.add(2, bz + a, bx + b, by + c, f3 * cum);
                 }
             }
         }
@@ -447,16 +496,14 @@ constexpr int BOX_CAP = 12288;
 // added to J once per non-zero node.  A chunk whose box exceeds BOX_CAP (unsorted particles,
 // a chunk across the periodic seam) deposits straight to global memory.
 template <int NDIM, int SHAPE>
-__global__ void __launch_bounds__(FUSED_T) push_deposit_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
-                                                               const float* __restrict__ B, float* __restrict__ J,
-                                                               int shift) {
-    extern __shared__ float sJ[];
-    __shared__ int box[6];
+__device__ __forceinline__ void push_deposit_chunks(const GridP& g, const SpeciesP& sp, const float* __restrict__ E,
+                                                    const float* __restrict__ B, float* __restrict__ J, int shift,
+                                                    long long chunk0, long long nchunk_stride, float* sJ, int* box) {
     constexpr int KW = Shape<SHAPE>::K + 1;
     const long long n = *sp.count;
     const long long cap = sp.cap;
     const int lane = threadIdx.x & 31;
-    for (long long base = (long long)blockIdx.x * FUSED_T; base < n; base += (long long)gridDim.x * FUSED_T) {
+    for (long long base = chunk0 * FUSED_T; base < n; base += nchunk_stride * FUSED_T) {
         if (threadIdx.x < 6) box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
         __syncthreads();
         const long long p = base + threadIdx.x;
@@ -491,21 +538,35 @@ __global__ void __launch_bounds__(FUSED_T) push_deposit_kernel(GridP g, SpeciesP
             const int v = (int)vol;
             for (int i = threadIdx.x; i < 3 * v; i += FUSED_T) sJ[i] = 0.f;
             __syncthreads();
-            if (ok) {
-                SharedAcc acc{sJ, box[0], box[2], box[4], zl, xl, v};
+            SharedAcc acc{sJ, box[0], box[2], box[4], zl, xl, v};
+            // one window for the whole warp (all lanes live, same window origin): warp-sum first
+            const unsigned live = __ballot_sync(0xffffffffu, ok);
+            // exact key: window origins are >= -2 and below 2^20 - 4 on every axis
+            unsigned long long key = ok ? (((unsigned long long)(lo[0] + 4) << 40) |
+                                           ((unsigned long long)(lo[1] + 4) << 20) |
+                                           (unsigned long long)(lo[2] + 4))
+                                        : ~0ull;
+            int same = 0;
+            __match_all_sync(0xffffffffu, key, &same);
+            if (live == 0xffffffffu && same) {
+                WarpSharedAcc wacc{acc, lane == 0};
+                deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, wacc);
+            } else if (ok) {
                 deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, acc);
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < 3 * v; i += FUSED_T) {
-                float val = sJ[i];
-                if (val == 0.f) continue;
-                int c = i / v, r = i - c * v;
-                int z = r % zl, q = r / zl;
-                int x = q % xl, y = q / xl;
-                int gz = box[0] + z;
-                if (gz < 0 || gz >= g.nz) continue;
-                long long o = ((long long)wrapi(box[4] + y, g.ny) * g.nx + wrapi(box[2] + x, g.nx)) * g.nz + gz;
-                atomicAdd(J + c * g.ncell + o, val);
+            // flush: one warp per z row of the box, lanes along z
+            const int rows = 3 * yl * xl;
+            for (int r = threadIdx.x >> 5; r < rows; r += FUSED_T >> 5) {
+                const int c = r / (yl * xl), q = r - c * (yl * xl);
+                const int y = q / xl, x = q - y * xl;
+                const int rowoff = c * (int)g.ncell + (wrapi(box[4] + y, g.ny) * g.nx + wrapi(box[2] + x, g.nx)) * g.nz;
+                const float* src = sJ + c * v + q * zl;
+                for (int z = lane; z < zl; z += 32) {
+                    float val = src[z];
+                    int gz = box[0] + z;
+                    if (val != 0.f && (unsigned)gz < (unsigned)g.nz) atomicAdd(J + rowoff + gz, val);
+                }
             }
         } else if (ok) {
             GlobalAcc acc{&g, J};
@@ -513,6 +574,315 @@ __global__ void __launch_bounds__(FUSED_T) push_deposit_kernel(GridP g, SpeciesP
         }
         __syncthreads();
     }
+}
+
+template <int NDIM, int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, NDIM == 3 ? 2 : 4) push_deposit_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
+                                                               const float* __restrict__ B, float* __restrict__ J,
+                                                               int shift) {
+    extern __shared__ float sJ[];
+    __shared__ int box[6];
+    push_deposit_chunks<NDIM, SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, sJ, box);
+}
+
+// Many independent runs: blockIdx.y selects the instance, blockIdx.x strides over its chunks.
+template <int NDIM, int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, NDIM == 3 ? 2 : 4) push_deposit_batch_kernel(const PartInst* __restrict__ inst,
+                                                                                        int parity) {
+    extern __shared__ float sJ[];
+    __shared__ int box[6];
+    const PartInst& q = inst[blockIdx.y];
+    const GridP g = prep_device(q.g);
+    push_deposit_chunks<NDIM, SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, sJ, box);
+}
+
+// ---------------------------------------------------------------- 2D fused kernel ----
+// Specialised 2D gather + push + Esirkepov for cell-sorted particles.  Per chunk of FUSED_T
+// particles (one per thread):
+//  1. the fields of the chunk's gather footprint are staged in shared memory (coalesced z rows,
+//     zero outside the z range), so the 6 x K^2 interpolation loads are shared-memory loads;
+//  2. the 2D Esirkepov weights are separable products of per-axis vectors:
+//       J1(a,b) = f1 Cz[a] Tx[b],  J2(a,b) = f2 Tz[a] Cx[b],
+//       J3(a,b) = qv v3 (S0z[a] (S0x[b] + dSx[b]/2) + dSz[a] (S0x[b]/2 + dSx[b]/3)),
+//     with Cz = cumsum dSz, Tx = S0x + dSx/2 (and z <-> x);
+//  3. lanes whose deposition windows start at the same node (runs of a cell-sorted warp) add
+//     their contributions with a segmented warp reduction first, so that only one lane per run
+//     issues the shared-memory atomic (dense beams otherwise serialise on the same addresses).
+// Boxes larger than the shared-memory caps fall back to global loads / global atomics.
+constexpr int F_CAP = 6 * 1536;    // field box floats (6 components)
+constexpr int J_CAP = 3 * 1536;    // current box floats (3 components)
+
+struct SegReduce {
+    bool same[5];       // lane + 2^k belongs to the same run
+    bool head;          // first lane of its run: adds the run's total
+    __device__ __forceinline__ float sum(float v) const {
+        float t;
+        t = __shfl_down_sync(0xffffffffu, v, 1);  if (same[0]) v += t;
+        t = __shfl_down_sync(0xffffffffu, v, 2);  if (same[1]) v += t;
+        t = __shfl_down_sync(0xffffffffu, v, 4);  if (same[2]) v += t;
+        t = __shfl_down_sync(0xffffffffu, v, 8);  if (same[3]) v += t;
+        t = __shfl_down_sync(0xffffffffu, v, 16); if (same[4]) v += t;
+        return v;
+    }
+};
+
+__device__ __forceinline__ SegReduce make_segments(unsigned long long key) {
+    const int lane = threadIdx.x & 31;
+    unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    SegReduce r;
+    r.head = lane == 0 || prev != key;
+    unsigned heads = __ballot_sync(0xffffffffu, r.head);
+    int run = __popc(heads & (0xffffffffu >> (31 - lane)));     // heads at or below this lane
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        int o = 1 << k;
+        int other = __shfl_down_sync(0xffffffffu, run, o);
+        r.same[k] = lane + o < 32 && other == run;
+    }
+    return r;
+}
+
+// block-wide min/max of lo/hi (two axes) into box[4]; all threads call
+__device__ __forceinline__ void box_reduce(int* box, int lz, int hz, int lx, int hx) {
+    const int lane = threadIdx.x & 31;
+    int a = __reduce_min_sync(0xffffffffu, lz), b = __reduce_max_sync(0xffffffffu, hz);
+    int c = __reduce_min_sync(0xffffffffu, lx), d = __reduce_max_sync(0xffffffffu, hx);
+    if (lane == 0 && a != INT_MAX) {
+        atomicMin(box + 0, a);
+        atomicMax(box + 1, b);
+        atomicMin(box + 2, c);
+        atomicMax(box + 3, d);
+    }
+}
+
+template <int SHAPE>
+__device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const SpeciesP& sp,
+                                                       const float* __restrict__ E, const float* __restrict__ B,
+                                                       float* __restrict__ J, int shift, long long chunk0,
+                                                       long long stride, float* sF, float* sJ, int* box) {
+    constexpr int K = Shape<SHAPE>::K;
+    constexpr int KW = K + 1;
+    const long long n = *sp.count;
+    const long long cap = sp.cap;
+    const int N = (int)g.ncell;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = FUSED_T / 32;
+    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T) {
+        if (threadIdx.x < 8) box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        __syncthreads();
+        const long long p = base + threadIdx.x;
+        // ---- load and decode ----
+        bool ok = false;
+        Pos p0;
+        float u[3] = {0.f, 0.f, 0.f};
+        if (p < n) {
+            int cell = sp.cell[p];
+            if (cell >= 0) {
+                int izg;
+                decode(g, cell, izg, p0.ix, p0.iy);
+                p0.iz = izg - 1 - shift;
+                if (p0.iz >= 0 && p0.iz < g.nz) {
+                    ok = true;
+                    p0.oz = sp.off[p];
+                    p0.ox = sp.off[cap + p];
+                    p0.oy = 0.f;
+                    u[0] = sp.u[p];
+                    u[1] = sp.u[cap + p];
+                    u[2] = sp.u[2 * cap + p];
+                } else {
+                    sp.cell[p] = -1;
+                }
+            }
+        }
+        // ---- gather weights and the chunk's field box ----
+        float Wzn[K], Wzh[K], Wxn[K], Wxh[K];
+        int bzn = 0, bzh = 0, bxn = 0, bxh = 0;
+        if (ok) {
+            bzn = p0.iz + Shape<SHAPE>::w(p0.oz, Wzn);
+            bzh = half_weights<SHAPE>(p0.iz, p0.oz, Wzh);
+            bxn = p0.ix + Shape<SHAPE>::w(p0.ox, Wxn);
+            bxh = half_weights<SHAPE>(p0.ix, p0.ox, Wxh);
+        }
+        box_reduce(box, ok ? min(bzn, bzh) : INT_MAX, ok ? max(bzn, bzh) + K - 1 : INT_MIN,
+                   ok ? min(bxn, bxh) : INT_MAX, ok ? max(bxn, bxh) + K - 1 : INT_MIN);
+        __syncthreads();
+        const bool any = box[0] != INT_MAX;
+        const int fz0 = box[0], fx0 = box[2];
+        const int fzl = any ? box[1] - box[0] + 1 : 0, fxl = any ? box[3] - box[2] + 1 : 0;
+        const int fvol = fzl * fxl;
+        const bool ftile = any && 6 * fvol <= F_CAP && fxl <= g.nx + 2 * K;
+        if (ftile) {
+            for (int r = warp; r < 6 * fxl; r += NW) {
+                const int c = r / fxl, x = r - c * fxl;
+                const float* src = (c < 3 ? E + c * N : B + (c - 3) * N) + wrapi(fx0 + x, g.nx) * g.nz;
+                float* dst = sF + c * fvol + x * fzl;
+                for (int z = lane; z < fzl; z += 32) {
+                    const int gz = fz0 + z;
+                    dst[z] = ((unsigned)gz < (unsigned)g.nz) ? __ldg(src + gz) : 0.f;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- gather (staggering: E1 z+, E2 x+, E3 node, B1 x+, B2 z+, B3 z+ x+) ----
+        float eb[6];
+        if (ok) {
+            if (ftile) {
+                auto tile = [&](int c, int bz, const float* Wz, int bx, const float* Wx) {
+                    const float* f = sF + c * fvol + (bx - fx0) * fzl + (bz - fz0);
+                    float acc = 0.f;
+#pragma unroll
+                    for (int b = 0; b < K; ++b) {
+                        float r = 0.f;
+#pragma unroll
+                        for (int a = 0; a < K; ++a) r += Wz[a] * f[b * fzl + a];
+                        acc += Wx[b] * r;
+                    }
+                    return acc;
+                };
+                eb[0] = tile(0, bzh, Wzh, bxn, Wxn);
+                eb[1] = tile(1, bzn, Wzn, bxh, Wxh);
+                eb[2] = tile(2, bzn, Wzn, bxn, Wxn);
+                eb[3] = tile(3, bzn, Wzn, bxh, Wxh);
+                eb[4] = tile(4, bzh, Wzh, bxn, Wxn);
+                eb[5] = tile(5, bzh, Wzh, bxh, Wxh);
+            } else {
+                gather<2, SHAPE>(g, E, B, p0, eb);
+            }
+        }
+        // ---- push and move ----
+        Pos p1 = p0;
+        float v3 = 0.f;
+        if (ok) {
+            boris(sp.eps, eb, u);
+            float gh, gl;
+            gamma_ff(u, gh, gl);
+            float dzh, dzl, dxh, dxl;
+            displacement(u[0], gh, gl, sp.kz[0], sp.kz[1], dzh, dzl);
+            displacement(u[1], gh, gl, sp.kx[0], sp.kx[1], dxh, dxl);
+            if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f)) {
+                ok = false;
+                sp.cell[p] = -1;
+            } else {
+                advance_axis(p1.iz, p1.oz, dzh, dzl);
+                advance_axis(p1.ix, p1.ox, dxh, dxl);
+                v3 = u[2] / gh;
+                const int wx = wrapi(p1.ix, g.nx);
+                sp.cell[p] = (p1.iz >= 0 && p1.iz < g.nz) ? encode(g, p1.iz, wx, 0) : -1;
+                sp.off[p] = p1.oz;
+                sp.off[cap + p] = p1.ox;
+                sp.u[p] = u[0];
+                sp.u[cap + p] = u[1];
+                sp.u[2 * cap + p] = u[2];
+            }
+        }
+        // ---- deposition vectors ----
+        float S0z[KW], DSz[KW], S0x[KW], DSx[KW];
+        int bz = 0, bx = 0;
+        if (ok) {
+            bz = axis_weights<SHAPE>(p0.iz, p0.oz, p1.iz, p1.oz, S0z, DSz);
+            bx = axis_weights<SHAPE>(p0.ix, p0.ox, p1.ix, p1.ox, S0x, DSx);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KW; ++k) S0z[k] = DSz[k] = S0x[k] = DSx[k] = 0.f;
+        }
+        if (threadIdx.x < 4) box[4 + threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        __syncthreads();
+        box_reduce(box + 4, ok ? bz : INT_MAX, ok ? bz + KW - 1 : INT_MIN, ok ? bx : INT_MAX, ok ? bx + KW - 1 : INT_MIN);
+        __syncthreads();
+        const int jz0 = box[4], jx0 = box[6];
+        const bool jany = jz0 != INT_MAX;
+        const int jzl = jany ? box[5] - jz0 + 1 : 0, jxl = jany ? box[7] - jx0 + 1 : 0;
+        const int jvol = jzl * jxl;
+        const bool jtile = jany && 3 * jvol <= J_CAP && jxl <= g.nx + 2 * KW;
+        if (jtile)
+            for (int i = threadIdx.x; i < 3 * jvol; i += FUSED_T) sJ[i] = 0.f;
+        __syncthreads();
+        if (jany) {
+            // runs of lanes with the same window
+            const unsigned long long key = ok ? (((unsigned long long)(bz + 4) << 32) | (unsigned)(bx + 4))
+                                              : (0xFFFFFFFF00000000ull | (unsigned)threadIdx.x);
+            const SegReduce seg = make_segments(key);
+            const float f1 = -sp.qv * g.dz / g.dt, f2 = -sp.qv * g.dx / g.dt, f3 = sp.qv * v3;
+            float Cz[KW], Tz[KW], Cx[KW], Tx[KW], Ax[KW], Bx[KW];
+            float cz = 0.f, cx = 0.f;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                cz += DSz[k];
+                cx += DSx[k];
+                Cz[k] = f1 * cz;
+                Cx[k] = f2 * cx;
+                Tz[k] = S0z[k] + 0.5f * DSz[k];
+                Tx[k] = S0x[k] + 0.5f * DSx[k];
+                Ax[k] = f3 * Tx[k];                                   // S0x + dSx/2
+                Bx[k] = f3 * (0.5f * S0x[k] + (1.f / 3.f) * DSx[k]);
+            }
+            auto put = [&](int c, int a, int b, float v) {
+                v = seg.sum(v);
+                if (seg.head && v != 0.f) {
+                    if (jtile) {
+                        atomicAdd(sJ + c * jvol + (bx + b - jx0) * jzl + (bz + a - jz0), v);
+                    } else {
+                        const int gz = bz + a;
+                        if ((unsigned)gz < (unsigned)g.nz) atomicAdd(J + c * N + wrapi(bx + b, g.nx) * g.nz + gz, v);
+                    }
+                }
+            };
+#pragma unroll
+            for (int b = 0; b < KW; ++b)
+#pragma unroll
+                for (int a = 0; a < KW; ++a) {
+                    if (a < KW - 1) put(0, a, b, Cz[a] * Tx[b]);
+                    if (b < KW - 1) put(1, a, b, Tz[a] * Cx[b]);
+                    put(2, a, b, S0z[a] * Ax[b] + DSz[a] * Bx[b]);
+                }
+        }
+        __syncthreads();
+        if (jtile) {
+            for (int r = warp; r < 3 * jxl; r += NW) {
+                const int c = r / jxl, x = r - c * jxl;
+                const float* src = sJ + c * jvol + x * jzl;
+                float* dst = J + c * N + wrapi(jx0 + x, g.nx) * g.nz;
+                for (int z = lane; z < jzl; z += 32) {
+                    const float val = src[z];
+                    const int gz = jz0 + z;
+                    if (val != 0.f && (unsigned)gz < (unsigned)g.nz) atomicAdd(dst + gz, val);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, 4) push_deposit_2d_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
+                                                                     const float* __restrict__ B, float* __restrict__ J,
+                                                                     int shift) {
+    extern __shared__ float smem[];
+    __shared__ int box[8];
+    push_deposit_2d_chunks<SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + F_CAP, box);
+}
+
+template <int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, 4) push_deposit_2d_batch_kernel(const PartInst* __restrict__ inst, int parity) {
+    extern __shared__ float smem[];
+    __shared__ int box[8];
+    const PartInst& q = inst[blockIdx.y];
+    const GridP g = prep_device(q.g);
+    push_deposit_2d_chunks<SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem, smem + F_CAP,
+                                  box);
+}
+
+// J = 0 for every instance (blockIdx.y) of a batch.
+__global__ void zero_j_batch_kernel(const PartInst* __restrict__ inst) {
+    const PartInst& q = inst[blockIdx.y];
+    const long long n = 3 * q.g.ncell;
+    float4* J4 = reinterpret_cast<float4*>(q.J);
+    const long long n4 = ((uintptr_t)q.J & 15) ? 0 : n / 4;   // vector stores only when aligned
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x)
+        J4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (long long i = 4 * n4 + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        q.J[i] = 0.f;
 }
 
 template <int NDIM, int SHAPE>
@@ -754,6 +1124,14 @@ cudaError_t dispatch(int ndim, int shape, F&& f) {
 }
 
 inline unsigned nblocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// the particle kernels decode cells with the magic-number divisions of the grid
+inline GridP prep(const GridP& g0) {
+    GridP g = g0;
+    g.div_nzg = make_fastdiv((uint32_t)g.nzg);
+    g.div_nx = make_fastdiv((uint32_t)g.nx);
+    return g;
+}
 // grid-stride kernels: enough CTAs for the expected extent, at most 16 per SM of a 152-SM part
 inline unsigned pblocks(long long extent) {
     long long b = (extent + 255) / 256;
@@ -762,12 +1140,23 @@ inline unsigned pblocks(long long extent) {
 
 }  // namespace
 
-cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, const float* B, float* J,
+cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, const float* B, float* J,
                         int shift, int mode, long long extent, cudaStream_t s) {
+    const GridP g = prep(g0);
     if (extent <= 0) return cudaSuccess;
     return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
         constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
-        if (mode == MODE_FUSED) {
+        if (mode == MODE_FUSED && ND == 2) {
+            auto k = push_deposit_2d_kernel<SH>;
+            const size_t smem = (F_CAP + J_CAP) * sizeof(float);
+            static bool configured = false;
+            if (!configured) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                configured = true;
+            }
+            k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift);
+        } else if (mode == MODE_FUSED) {
             auto k = push_deposit_kernel<ND, SH>;
             static bool configured = false;
             if (!configured) {
@@ -784,8 +1173,49 @@ cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, cons
     });
 }
 
-cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J, long long extent,
+cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int shape, long long max_extent, int parity,
+                              cudaStream_t s) {
+    if (ninst <= 0) return cudaSuccess;
+    long long b = (max_extent + FUSED_T - 1) / FUSED_T;
+    dim3 grid((unsigned)(b < 1 ? 1 : (b > 64 ? 64 : b)), (unsigned)ninst);
+    return dispatch(ndim, shape, [&](auto nd, auto sh) {
+        constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
+        if (ND == 2) {
+            auto k = push_deposit_2d_batch_kernel<SH>;
+            const size_t smem = (F_CAP + J_CAP) * sizeof(float);
+            static bool configured = false;
+            if (!configured) {
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                configured = true;
+            }
+            k<<<grid, FUSED_T, smem, s>>>(inst, parity);
+            return cudaGetLastError();
+        }
+        auto k = push_deposit_batch_kernel<ND, SH>;
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(BOX_CAP * sizeof(float)));
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        k<<<grid, FUSED_T, BOX_CAP * sizeof(float), s>>>(inst, parity);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t launch_zero_j_batch(const PartInst* inst, int ninst, long long max_ncell, cudaStream_t s) {
+    if (ninst <= 0) return cudaSuccess;
+    long long b = (3 * max_ncell / 4 + 255) / 256;
+    dim3 grid((unsigned)(b < 1 ? 1 : (b > 64 ? 64 : b)), (unsigned)ninst);
+    zero_j_batch_kernel<<<grid, 256, 0, s>>>(inst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_deposit_unfused(const GridP& g0, const SpeciesP& sp, float* J, long long extent,
                                    cudaStream_t s) {
+    const GridP g = prep(g0);
     if (extent <= 0) return cudaSuccess;
     return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
         constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
@@ -832,8 +1262,9 @@ cudaError_t launch_sort(const GridP& g, const SpeciesP& sp, long long extent, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_rho(const GridP& g, const SpeciesP& sp, int shift, double* rho, long long extent,
+cudaError_t launch_rho(const GridP& g0, const SpeciesP& sp, int shift, double* rho, long long extent,
                        cudaStream_t s) {
+    const GridP g = prep(g0);
     if (extent <= 0) return cudaSuccess;
     return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
         constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;

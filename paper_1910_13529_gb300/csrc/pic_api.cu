@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <algorithm>
 #include <vector>
 
 #include "pic_internal.h"
@@ -63,6 +64,8 @@ struct pic_t {
     std::vector<int> ev_cat;
     size_t ev_used = 0;
     long long launches[PIC_TIMING_N] = {0};
+    int fa_variant = 0;           // field-advance tile variant (pic_autotune)
+    double fa_ms[8] = {0};        // measured time per variant (ms), 0 = not measured
 };
 
 namespace {
@@ -193,7 +196,7 @@ pic_status advance_fields(pic_t* h, const float* Ein, const float* Bin, float* E
     p.shift = shift;
     {
         Scope sc(h, PIC_T_FIELDS, 1, s);
-        CK(h, launch_field_advance(p, s), "field advance kernel");
+        CK(h, launch_field_advance(p, s, h->fa_variant), "field advance kernel");
     }
     h->step = n_done;
     if (shift) {
@@ -684,6 +687,318 @@ pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream
         if (ms) ms[c] = acc[c];
         if (launches) launches[c] = h->launches[c];
     }
+    return PIC_OK;
+}
+
+// Tile autotuner: time every field-advance tile variant on this handle's bound fields (the
+// output goes to the library's second buffer, so the state is unchanged) and keep the fastest.
+// The choice is cached per (ndim, stencil class, nz, nx, ny) for the process.
+pic_status pic_autotune(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    static std::vector<std::pair<std::vector<long long>, int>> cache;
+    const int mclass = h->st.M <= 1 ? 1 : h->st.M <= 4 ? 4 : h->st.M <= 8 ? 8 : 16;
+    std::vector<long long> key = {h->g.ndim, mclass, h->g.nz, h->g.nx, h->g.ny};
+    for (auto& e : cache)
+        if (e.first == key) {
+            h->fa_variant = e.second;
+            return PIC_OK;
+        }
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long N = h->g.ncell;
+    FieldP p;
+    p.g = h->g;
+    p.st = h->st;
+    p.Ein = h->E;
+    p.Bin = h->B;
+    p.J1 = h->J;
+    p.J2 = h->J + N;
+    p.J3 = h->J + 2 * N;
+    p.Eout = h->E2;
+    p.Bout = h->B2;
+    p.shift = 0;
+    cudaEvent_t a, b;
+    CK(h, cudaEventCreate(&a), "event");
+    CK(h, cudaEventCreate(&b), "event");
+    int best = 0;
+    double best_ms = 1e30;
+    const int nv = field_variants(h->g.ndim);
+    for (int v = 0; v < nv; ++v) {
+        cudaError_t e = launch_field_advance(p, s, v);          // warm-up (and attribute set-up)
+        for (int r = 0; e == cudaSuccess && r < 2; ++r) e = launch_field_advance(p, s, v);
+        if (e == cudaSuccess) e = cudaEventRecord(a, s);
+        for (int r = 0; e == cudaSuccess && r < 5; ++r) e = launch_field_advance(p, s, v);
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return cuda_fail(h, e, "autotune");
+        }
+        h->fa_ms[v] = ms / 5.0;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->fa_variant = best;
+    cache.push_back({key, best});
+    return PIC_OK;
+}
+
+pic_status pic_get_tuning(const pic_t* h, int* variant, double* ms, int* nvariants) {
+    if (!h) return PIC_ERR_ARG;
+    if (variant) *variant = h->fa_variant;
+    int nv = field_variants(h->g.ndim);
+    if (nvariants) *nvariants = nv;
+    if (ms)
+        for (int v = 0; v < nv; ++v) ms[v] = h->fa_ms[v];
+    return PIC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batched runs ----
+struct pic_batch_t {
+    std::vector<pic_t*> h;
+    // per field-class tables (index: stencil class 0..3 = M <= 1, 4, 8, 16)
+    struct FieldGroup {
+        std::vector<int> members;
+        FieldP* d_inst = nullptr;
+        int* d_tiles = nullptr;
+        int total = 0, maxm = 1;
+    } fg[4];
+    struct PartGroup {
+        std::vector<int> members;
+        PartInst* d_inst = nullptr;
+        long long max_extent = 0, max_ncell = 0;
+        int shape = 1;
+    } pg[2];            // shape 1, 2
+    CorrInst* d_corr = nullptr;
+    int ncorr = 0, max_rows = 0, max_nz = 0;
+    int ndim = 2;
+    bool built = false;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    char err[256] = {0};
+};
+
+namespace {
+
+int stencil_class(int M) { return M <= 1 ? 0 : M <= 4 ? 1 : M <= 8 ? 2 : 3; }
+
+template <typename T>
+cudaError_t upload(T** d, const std::vector<T>& v) {
+    if (*d) cudaFree(*d);
+    *d = nullptr;
+    if (v.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void**)d, sizeof(T) * v.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+}
+
+pic_status bfail(pic_batch_t* b, pic_status st, const char* what) {
+    snprintf(b->err, sizeof b->err, "%s", what);
+    snprintf(g_create_err, sizeof g_create_err, "%s", what);
+    return st;
+}
+
+// device tables of a batch (after all instances are bound)
+pic_status batch_build(pic_batch_t* b) {
+    for (auto& f : b->fg) f.members.clear();
+    for (auto& q : b->pg) q.members.clear();
+    std::vector<CorrInst> corr;
+    b->max_rows = b->max_nz = 0;
+    for (int i = 0; i < (int)b->h.size(); ++i) {
+        pic_t* h = b->h[i];
+        if (!h->E || !h->sp[0].bound) return bfail(b, PIC_ERR_STATE, "batch instance not bound (fields and species 0)");
+        b->fg[stencil_class(h->st.M)].members.push_back(i);
+        b->pg[h->cfg.shape - 1].members.push_back(i);
+        if (h->hlen > 0) {
+            CorrInst c;
+            c.g = h->g;
+            c.hlen = h->hlen;
+            for (int k = 0; k < 2 * PIC_MAX_HLEN + 1; ++k) c.h[k] = k < 2 * h->hlen + 1 ? h->hf[k] : 0.f;
+            c.J1 = h->J;
+            corr.push_back(c);
+            long long rows = (long long)h->g.nx * h->g.ny;
+            if (rows > b->max_rows) b->max_rows = (int)rows;
+            if (h->g.nz > b->max_nz) b->max_nz = h->g.nz;
+        }
+    }
+    static const int maxm_of[4] = {1, 4, 8, 16};
+    for (int c = 0; c < 4; ++c) {
+        auto& f = b->fg[c];
+        std::vector<FieldP> inst;
+        std::vector<int> tiles(1, 0);
+        for (int i : f.members) {
+            pic_t* h = b->h[i];
+            for (int par = 0; par < 2; ++par) {
+                FieldP p;
+                p.g = h->g;
+                p.st = h->st;
+                p.Ein = par ? h->E2 : h->E;
+                p.Bin = par ? h->B2 : h->B;
+                p.J1 = h->J;
+                p.J2 = h->J + h->g.ncell;
+                p.J3 = h->J + 2 * h->g.ncell;
+                p.Eout = par ? h->E : h->E2;
+                p.Bout = par ? h->B : h->B2;
+                p.shift = 0;
+                inst.push_back(p);
+            }
+            tiles.push_back(tiles.back() + field_tiles(b->ndim, maxm_of[c], h->g.nz, h->g.nx, h->g.ny));
+        }
+        f.total = tiles.back();
+        f.maxm = maxm_of[c];
+        if (upload(&f.d_inst, inst) != cudaSuccess || upload(&f.d_tiles, tiles) != cudaSuccess)
+            return bfail(b, PIC_ERR_OOM, "batch field tables");
+    }
+    for (int sh = 0; sh < 2; ++sh) {
+        auto& q = b->pg[sh];
+        std::vector<PartInst> inst;
+        q.max_extent = q.max_ncell = 0;
+        q.shape = sh + 1;
+        for (int i : q.members) {
+            pic_t* h = b->h[i];
+            PartInst p;
+            p.g = h->g;
+            p.sp = species_params(h, 0);
+            p.E[0] = h->E;
+            p.E[1] = h->E2;
+            p.B[0] = h->B;
+            p.B[1] = h->B2;
+            p.J = h->J;
+            inst.push_back(p);
+            q.max_extent = std::max(q.max_extent, h->sp[0].extent);
+            q.max_ncell = std::max(q.max_ncell, h->g.ncell);
+        }
+        if (upload(&q.d_inst, inst) != cudaSuccess) return bfail(b, PIC_ERR_OOM, "batch particle tables");
+    }
+    b->ncorr = (int)corr.size();
+    if (upload(&b->d_corr, corr) != cudaSuccess) return bfail(b, PIC_ERR_OOM, "batch correction table");
+    b->built = true;
+    return PIC_OK;
+}
+
+// one step of every instance, reading the field buffers of this parity
+cudaError_t batch_enqueue_step(pic_batch_t* b, int parity, cudaStream_t s) {
+    cudaError_t e;
+    for (auto& q : b->pg)
+        if (!q.members.empty() && (e = launch_zero_j_batch(q.d_inst, (int)q.members.size(), q.max_ncell, s))) return e;
+    for (auto& q : b->pg)
+        if (!q.members.empty() &&
+            (e = launch_push_batch(q.d_inst, (int)q.members.size(), b->ndim, q.shape, q.max_extent, parity, s)))
+            return e;
+    if (b->ncorr && (e = launch_correct_j1_batch(b->d_corr, b->ncorr, b->max_rows, b->max_nz, s))) return e;
+    for (auto& f : b->fg)
+        if (!f.members.empty() &&
+            (e = launch_field_advance_batch(f.d_inst, f.d_tiles, (int)f.members.size(), f.total, b->ndim, f.maxm,
+                                            parity, s)))
+            return e;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+pic_status pic_batch_create(const pic_config* cfgs, int n, pic_batch_t** out) {
+    if (!cfgs || !out || n < 1) return fail(nullptr, PIC_ERR_ARG, "pic_batch_create: need n >= 1 configs");
+    *out = nullptr;
+    pic_batch_t* b = new (std::nothrow) pic_batch_t();
+    if (!b) return fail(nullptr, PIC_ERR_OOM, "host allocation");
+    b->ndim = cfgs[0].ndim;
+    for (int i = 0; i < n; ++i) {
+        if (cfgs[i].moving_window || cfgs[i].sort_every || cfgs[i].ndim != b->ndim) {
+            pic_batch_destroy(b);
+            return fail(nullptr, PIC_ERR_ARG, "batch instance %d: same ndim for all, no moving window, no sort", i);
+        }
+        pic_t* h = nullptr;
+        pic_status st = pic_create(&cfgs[i], &h);
+        if (st) {
+            char msg[256];
+            snprintf(msg, sizeof msg, "batch instance %d: %s", i, g_create_err);
+            snprintf(g_create_err, sizeof g_create_err, "%s", msg);
+            pic_batch_destroy(b);
+            return st;
+        }
+        b->h.push_back(h);
+    }
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        pic_batch_destroy(b);
+        return fail(nullptr, PIC_ERR_CUDA, "batch capture stream");
+    }
+    *out = b;
+    return PIC_OK;
+}
+
+pic_status pic_batch_instance(pic_batch_t* b, int i, pic_t** h) {
+    if (!b || !h || i < 0 || i >= (int)b->h.size()) return PIC_ERR_ARG;
+    *h = b->h[i];
+    b->built = false;            // bindings may change: rebuild tables and graph at the next step
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_batch_step(pic_batch_t* b, int nsteps, void* stream) {
+    if (!b || nsteps < 0) return PIC_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!b->built) {
+        pic_status st = batch_build(b);
+        if (st) return st;
+    }
+    if (!b->graph) {
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t e1 = batch_enqueue_step(b, 0, b->cap);
+            cudaError_t e2 = batch_enqueue_step(b, 1, b->cap);
+            e = cudaStreamEndCapture(b->cap, &g);
+            if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (int k = 0; k + 1 < nsteps; k += 2) {
+        cudaError_t e = cudaGraphLaunch(b->graph, s);
+        if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    if (nsteps % 2) {
+        cudaError_t e = batch_enqueue_step(b, 0, s);
+        for (pic_t* h : b->h) {
+            if (e != cudaSuccess) break;
+            const size_t bytes = sizeof(float) * 3 * h->g.ncell;
+            e = cudaMemcpyAsync(h->E, h->E2, bytes, cudaMemcpyDeviceToDevice, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h->B, h->B2, bytes, cudaMemcpyDeviceToDevice, s);
+        }
+        if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
+    }
+    for (pic_t* h : b->h) h->step += nsteps;
+    return PIC_OK;
+}
+
+pic_status pic_batch_destroy(pic_batch_t* b) {
+    if (!b) return PIC_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (auto& f : b->fg) {
+        dfree(f.d_inst);
+        dfree(f.d_tiles);
+    }
+    for (auto& q : b->pg) dfree(q.d_inst);
+    dfree(b->d_corr);
+    for (pic_t* h : b->h) pic_destroy(h);
+    delete b;
     return PIC_OK;
 }
 

@@ -8,6 +8,23 @@
 
 namespace pic {
 
+// Division by a run-time constant d without an integer divide (Granlund-Montgomery):
+// n / d = (t + ((n - t) >> 1)) >> (s - 1), t = umulhi(m, n), for all 32-bit n.
+struct FastDiv {
+    uint32_t d, m;
+    int s;   // -1: d == 1
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f{d, 0u, -1};
+    if (d <= 1) return f;
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    f.m = (uint32_t)((((1ull << 32) * ((1ull << l) - d)) / d) + 1);
+    f.s = l;
+    return f;
+}
+
 // Grid constants passed by value to every kernel.
 struct GridP {
     int ndim;
@@ -16,6 +33,7 @@ struct GridP {
     long long ncell;    // nz * nx * ny
     float dz, dx, dy, dt;
     int shape;          // 1 or 2
+    FastDiv div_nzg, div_nx;   // filled by the particle launchers
 };
 
 // Axial stencil (Appendix C).  M = 1, C[0] = 1 is the Yee difference.
@@ -55,12 +73,38 @@ struct SpeciesP {
     float* prev_off;
 };
 
+// One instance of a batched run: its grid, its (single) species, its two field buffers.
+struct PartInst {
+    GridP g;
+    SpeciesP sp;
+    const float* E[2];   // fields read at even / odd steps
+    const float* B[2];
+    float* J;
+};
+
+// Current correction of one instance (customised stencil).
+struct CorrInst {
+    GridP g;
+    float h[2 * PIC_MAX_HLEN + 1];
+    int hlen;
+    float* J1;
+};
+
 // Device status word bits.
 enum : int { STATUS_CAPACITY = 1, STATUS_TIMEOUT = 2 };
 
 // ---- launchers (return cudaGetLastError of the launch) ----
-cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s);
+cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s, int variant = 0);
+int field_variants(int ndim);
 cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s);
+// batched: instance tables live in device memory
+cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,
+                                       int ndim, int maxm, int parity, cudaStream_t s);
+int field_tiles(int ndim, int maxm, int nz, int nx, int ny);
+cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_rows, int max_nz, cudaStream_t s);
+cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int shape, long long max_extent, int parity,
+                              cudaStream_t s);
+cudaError_t launch_zero_j_batch(const PartInst* inst, int ninst, long long max_ncell, cudaStream_t s);
 cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, const float* B,
                         float* J, int shift, int mode, long long extent, cudaStream_t s);
 cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J, long long extent,

@@ -5,7 +5,8 @@ import ctypes
 import numpy as np
 import torch
 
-from . import (PIC_SOLVER_CUSTOM, PIC_SOLVER_YEE, encode_cells, pic_bind_fields, pic_bind_species,
+from . import (PIC_SOLVER_CUSTOM, PIC_SOLVER_YEE, encode_cells, pic_batch_create, pic_batch_destroy,
+               pic_batch_instance, pic_batch_step, pic_bind_fields, pic_bind_species,
                pic_config, pic_create, pic_deposit, pic_destroy, pic_diag, pic_field_advance,
                pic_gather_push, pic_gauss, pic_get_coefficients, pic_get_count, pic_get_state, pic_rho,
                pic_sort, pic_step, pic_sync)
@@ -38,7 +39,7 @@ def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee"
 class Simulation:
     """One libpic handle with its fields and species held in torch CUDA tensors."""
 
-    def __init__(self, device="cuda:0", **cfg):
+    def __init__(self, device="cuda:0", handle=None, **cfg):
         if not torch.cuda.is_available():
             raise RuntimeError("libpic needs a CUDA device")
         self.device = torch.device(device)
@@ -46,7 +47,8 @@ class Simulation:
         self.cfg = dict(cfg)
         c, keep = make_config(**cfg)
         self._c, self._keep = c, keep
-        self.h = pic_create(c)
+        self.owned = handle is None
+        self.h = pic_create(c) if handle is None else handle
         self.ndim, self.nz, self.nx, self.ny = c.ndim, c.nz, c.nx, c.ny
         shp = (3, self.ny, self.nx, self.nz)
         self.E = torch.zeros(shp, dtype=torch.float32, device=self.device)
@@ -133,8 +135,40 @@ class Simulation:
     def close(self):
         if self.h is not None:
             torch.cuda.synchronize(self.device)
-            pic_destroy(self.h)
+            if self.owned:
+                pic_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """A libpic batch: many independent runs advanced together (pic_batch_step).  Each instance
+    is a Simulation view over the batch's instance handle."""
+
+    def __init__(self, cfgs, device="cuda:0"):
+        self.device = torch.device(device)
+        torch.cuda.set_device(self.device)
+        made = [make_config(**c) for c in cfgs]
+        self._keep = made
+        self.b = pic_batch_create([m[0] for m in made])
+        self.instances = [Simulation(device=device, handle=pic_batch_instance(self.b, i), **cfgs[i])
+                          for i in range(len(cfgs))]
+
+    def step(self, n=1):
+        pic_batch_step(self.b, n, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream))
+
+    def close(self):
+        if self.b is not None:
+            torch.cuda.synchronize(self.device)
+            for s in self.instances:
+                s.h = None
+            pic_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:
