@@ -153,7 +153,8 @@ pic_status pic_gather_push(pic_t* h, void* stream);
 pic_status pic_deposit(pic_t* h, void* stream);
 pic_status pic_field_advance(pic_t* h, void* stream);
 pic_status pic_step(pic_t* h, int nsteps, void* stream);
-/* Counting sort of every species by cell (dead slots removed); ids follow their particles. */
+/* Counting sort of every species (dead slots removed; ids follow their particles).  Order: 8 x 8
+ * tiles of (z, x) cells, tiles z-fastest then x (then y), cells z-fastest inside a tile. */
 pic_status pic_sort(pic_t* h, void* stream);
 
 /* ---- diagnostics (FP64 on the GPU) ----------------------------------------------------
@@ -191,6 +192,13 @@ pic_status pic_gauss_static(pic_t* h, double* G, void* stream);
 pic_status pic_get_count(pic_t* h, int s, int64_t* n, void* stream);
 /* Completed steps, window shifts, and whether a shift is still pending on the particles. */
 pic_status pic_get_state(const pic_t* h, int64_t* step, int64_t* shifts, int* pending_shift);
+/* Next id given to an injected particle. */
+pic_status pic_get_next_id(const pic_t* h, int64_t* next_id);
+/* Restore the counters of a saved run (checkpoint/resume): completed steps, window shifts,
+ * whether a shift is pending on the particles, and the next injected particle id.  The
+ * fields and particles themselves are the caller's arrays (rebind the species to set counts). */
+pic_status pic_set_state(pic_t* h, int64_t step, int64_t shifts, int pending_shift, int64_t next_id);
+
 /* Synchronise stream and report any CUDA or device-side error. */
 pic_status pic_sync(pic_t* h, void* stream);
 
@@ -212,6 +220,20 @@ enum {
 pic_status pic_timing(pic_t* h, int enable);
 pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream);
 
+/* ---- adjoint of the field step (gradients with respect to the axial coefficients) ---------
+ * For a loss L of the fields after some steps, with particle currents that do not depend on the
+ * fields (a rigidly moving beam), pic_adjoint_step takes the adjoint (aE, aB) = dL/d(E, B) at
+ * the end of one step back to the start of that step and adds the step's contribution to
+ * dL/dC_l (the Sec. 3 / Appendix C axial coefficients, including their effect through the
+ * Sec. 3 current correction) to grad.
+ *   E, B:   forward fields at the start of the step (device, 3 nz nx ny floats each);
+ *   J:      the (corrected) current of that step, as pic_step / pic_deposit left it in J;
+ *   aE, aB: device, updated in place; grad: device double[M], accumulated (not cleared).
+ * The transposed operators use d-x = (d+x)^T (the pair of Appendix C), so the adjoint step is
+ * the leapfrog with the roles of d+ and d- exchanged.  Library scratch: 7 nz nx ny floats.  */
+pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const float* J, float* aE, float* aB,
+                            double* grad, void* stream);
+
 /* ---- tile autotuner ----------------------------------------------------------------------
  * pic_autotune times each field-advance tile variant on the handle's bound fields (results go
  * to library scratch; the state is unchanged; synchronises stream) and keeps the fastest for
@@ -220,6 +242,8 @@ pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream
  * and the number of variants (2D: 128x8, 256x4, 64x16, 256x8; 3D: 64x4x4, 128x4x2, 32x8x4).  */
 pic_status pic_autotune(pic_t* h, void* stream);
 pic_status pic_get_tuning(const pic_t* h, int* variant, double* ms, int* nvariants);
+/* Force a field-advance tile variant (0 <= variant < nvariants). */
+pic_status pic_set_tuning(pic_t* h, int variant);
 
 /* ---- batched runs: many independent instances per launch --------------------------------
  * A batch holds n independent 2D or 3D runs (no moving window, no sort), each with its own

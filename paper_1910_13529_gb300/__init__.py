@@ -28,7 +28,8 @@ EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients"
            "pic_deposit", "pic_field_advance", "pic_step", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
            "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
            "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy",
-           "pic_autotune", "pic_get_tuning"]
+           "pic_autotune", "pic_get_tuning", "pic_set_tuning", "pic_adjoint_step",
+           "pic_set_state", "pic_get_next_id"]
 TIMING_KEYS = ["particles", "deposit", "correction", "fields", "sort", "window", "diag"]
 
 
@@ -87,6 +88,10 @@ def _load():
         "pic_batch_destroy": ([vp], ctypes.c_int),
         "pic_autotune": ([vp, vp], ctypes.c_int),
         "pic_get_tuning": ([vp, ip, dp, ip], ctypes.c_int),
+        "pic_set_tuning": ([vp, ctypes.c_int], ctypes.c_int),
+        "pic_adjoint_step": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "pic_set_state": ([vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+        "pic_get_next_id": ([vp, i64p], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -247,6 +252,24 @@ def pic_get_tuning(h):
     ms = np.zeros(8)
     _check(lib.pic_get_tuning(h, ctypes.byref(v), _dptr(ms), ctypes.byref(nv)), h)
     return v.value, ms[: nv.value]
+
+
+def pic_set_tuning(h, variant):
+    _check(lib.pic_set_tuning(h, int(variant)), h)
+
+
+def pic_adjoint_step(h, E_ptr, B_ptr, J_ptr, aE_ptr, aB_ptr, grad_ptr, stream):
+    _check(lib.pic_adjoint_step(h, E_ptr, B_ptr, J_ptr, aE_ptr, aB_ptr, grad_ptr, stream), h)
+
+
+def pic_set_state(h, step, shifts, pending_shift, next_id):
+    _check(lib.pic_set_state(h, int(step), int(shifts), int(pending_shift), int(next_id)), h)
+
+
+def pic_get_next_id(h):
+    n = ctypes.c_int64()
+    _check(lib.pic_get_next_id(h, ctypes.byref(n)), h)
+    return n.value
 
 
 def pic_batch_create(cfgs):

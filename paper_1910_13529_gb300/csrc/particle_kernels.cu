@@ -228,8 +228,10 @@ __device__ __forceinline__ void gamma_ff(const float* u, float& gh, float& gl) {
 // drift by the same fraction of an ulp every step.
 __device__ __forceinline__ void displacement(float ua, float gh, float gl, float kh, float kl, float& dh,
                                              float& dl) {
-    float qh = ua / gh;
-    float ql = (fmaf(-qh, gh, ua) - qh * gl) / gh;
+    // one reciprocal; the exact FMA residual ua - qh gh corrects whatever rounding qh carries
+    const float rg = __frcp_rn(gh);
+    float qh = ua * rg;
+    float ql = (fmaf(-qh, gh, ua) - qh * gl) * rg;
     dh = qh * kh;
     dl = fmaf(qh, kh, -dh) + (qh * kl + ql * kh);
 }
@@ -306,18 +308,20 @@ __device__ __forceinline__ int axis_weights(int i0, float o0, int i1, float o1, 
     constexpr int K = Shape<SHAPE>::K;
     constexpr int KW = K + 1;
     float w0[K], w1[K];
-    int b0 = i0 + Shape<SHAPE>::w(o0, w0);
-    int b1 = i1 + Shape<SHAPE>::w(o1, w1);
-    int b = min(b0, b1);
-    int s0 = b0 - b, s1 = b1 - b;
+    const int b0 = i0 + Shape<SHAPE>::w(o0, w0);
+    const int b1 = i1 + Shape<SHAPE>::w(o1, w1);
+    // the supports start at most one node apart: place each at offset 0 or 1 of the window
+    const bool sh0 = b0 > b1, sh1 = b1 > b0;
 #pragma unroll
     for (int k = 0; k < KW; ++k) {
-        float a = (k - s0 >= 0 && k - s0 < K) ? w0[k - s0] : 0.f;
-        float c = (k - s1 >= 0 && k - s1 < K) ? w1[k - s1] : 0.f;
+        const float a0 = k < K ? w0[k] : 0.f, a1 = k >= 1 ? w0[k - 1] : 0.f;
+        const float c0 = k < K ? w1[k] : 0.f, c1 = k >= 1 ? w1[k - 1] : 0.f;
+        const float a = sh0 ? a1 : a0;
+        const float c = sh1 ? c1 : c0;
         S0[k] = a;
         DS[k] = c - a;
     }
-    return b;
+    return min(b0, b1);
 }
 
 // Esirkepov current of one particle moving p0 -> p1 (|displacement| < 1 cell per axis).
@@ -615,13 +619,14 @@ constexpr int J_CAP = 3 * 1536;    // current box floats (3 components)
 struct SegReduce {
     bool same[5];       // lane + 2^k belongs to the same run
     bool head;          // first lane of its run: adds the run's total
+    int steps;          // warp-uniform: ceil(log2(longest run)), 0 when no lanes share a window
     __device__ __forceinline__ float sum(float v) const {
         float t;
-        t = __shfl_down_sync(0xffffffffu, v, 1);  if (same[0]) v += t;
-        t = __shfl_down_sync(0xffffffffu, v, 2);  if (same[1]) v += t;
-        t = __shfl_down_sync(0xffffffffu, v, 4);  if (same[2]) v += t;
-        t = __shfl_down_sync(0xffffffffu, v, 8);  if (same[3]) v += t;
-        t = __shfl_down_sync(0xffffffffu, v, 16); if (same[4]) v += t;
+        if (steps > 0) { t = __shfl_down_sync(0xffffffffu, v, 1);  if (same[0]) v += t; }
+        if (steps > 1) { t = __shfl_down_sync(0xffffffffu, v, 2);  if (same[1]) v += t; }
+        if (steps > 2) { t = __shfl_down_sync(0xffffffffu, v, 4);  if (same[2]) v += t; }
+        if (steps > 3) { t = __shfl_down_sync(0xffffffffu, v, 8);  if (same[3]) v += t; }
+        if (steps > 4) { t = __shfl_down_sync(0xffffffffu, v, 16); if (same[4]) v += t; }
         return v;
     }
 };
@@ -631,8 +636,13 @@ __device__ __forceinline__ SegReduce make_segments(unsigned long long key) {
     unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
     SegReduce r;
     r.head = lane == 0 || prev != key;
-    unsigned heads = __ballot_sync(0xffffffffu, r.head);
-    int run = __popc(heads & (0xffffffffu >> (31 - lane)));     // heads at or below this lane
+    const unsigned heads = __ballot_sync(0xffffffffu, r.head);
+    // run length of a head: distance to the next head (or to the end of the warp)
+    const unsigned above = lane < 31 ? (heads >> (lane + 1)) : 0u;
+    const int len = r.head ? (above ? __ffs(above) : 32 - lane) : 0;
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    r.steps = maxlen <= 1 ? 0 : 32 - __clz(maxlen - 1);
+    const int run = __popc(heads & (0xffffffffu >> (31 - lane)));     // heads at or below this lane
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         int o = 1 << k;
@@ -653,6 +663,23 @@ __device__ __forceinline__ void box_reduce(int* box, int lz, int hz, int lx, int
         atomicMin(box + 2, c);
         atomicMax(box + 3, d);
     }
+}
+
+// K x K interpolation from a shared-memory box (rows of length zl along z)
+template <int K>
+__device__ __forceinline__ float tile_interp(const float* __restrict__ f, int zl, int z, int x, const float (&Wz)[K],
+                                             const float (&Wx)[K]) {
+    const float* r = f + x * zl + z;
+    float acc = 0.f;
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+        float t = 0.f;
+#pragma unroll
+        for (int a = 0; a < K; ++a) t = fmaf(Wz[a], r[a], t);
+        acc = fmaf(Wx[b], t, acc);
+        r += zl;
+    }
+    return acc;
 }
 
 template <int SHAPE>
@@ -727,24 +754,12 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
         float eb[6];
         if (ok) {
             if (ftile) {
-                auto tile = [&](int c, int bz, const float* Wz, int bx, const float* Wx) {
-                    const float* f = sF + c * fvol + (bx - fx0) * fzl + (bz - fz0);
-                    float acc = 0.f;
-#pragma unroll
-                    for (int b = 0; b < K; ++b) {
-                        float r = 0.f;
-#pragma unroll
-                        for (int a = 0; a < K; ++a) r += Wz[a] * f[b * fzl + a];
-                        acc += Wx[b] * r;
-                    }
-                    return acc;
-                };
-                eb[0] = tile(0, bzh, Wzh, bxn, Wxn);
-                eb[1] = tile(1, bzn, Wzn, bxh, Wxh);
-                eb[2] = tile(2, bzn, Wzn, bxn, Wxn);
-                eb[3] = tile(3, bzn, Wzn, bxh, Wxh);
-                eb[4] = tile(4, bzh, Wzh, bxn, Wxn);
-                eb[5] = tile(5, bzh, Wzh, bxh, Wxh);
+                eb[0] = tile_interp<K>(sF + 0 * fvol, fzl, bzh - fz0, bxn - fx0, Wzh, Wxn);
+                eb[1] = tile_interp<K>(sF + 1 * fvol, fzl, bzn - fz0, bxh - fx0, Wzn, Wxh);
+                eb[2] = tile_interp<K>(sF + 2 * fvol, fzl, bzn - fz0, bxn - fx0, Wzn, Wxn);
+                eb[3] = tile_interp<K>(sF + 3 * fvol, fzl, bzn - fz0, bxh - fx0, Wzn, Wxh);
+                eb[4] = tile_interp<K>(sF + 4 * fvol, fzl, bzh - fz0, bxn - fx0, Wzh, Wxn);
+                eb[5] = tile_interp<K>(sF + 5 * fvol, fzl, bzh - fz0, bxh - fx0, Wzh, Wxh);
             } else {
                 gather<2, SHAPE>(g, E, B, p0, eb);
             }
@@ -816,15 +831,21 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
                 Ax[k] = f3 * Tx[k];                                   // S0x + dSx/2
                 Bx[k] = f3 * (0.5f * S0x[k] + (1.f / 3.f) * DSx[k]);
             }
+            // shared box: the lane's window origin in the box; global fallback: wrapped row offsets
+            const int sbase = (bx - jx0) * jzl + (bz - jz0);
+            int grow[KW];
+#pragma unroll
+            for (int b = 0; b < KW; ++b) grow[b] = wrapi(bx + b, g.nx) * g.nz;
             auto put = [&](int c, int a, int b, float v) {
                 v = seg.sum(v);
-                if (seg.head && v != 0.f) {
-                    if (jtile) {
-                        atomicAdd(sJ + c * jvol + (bx + b - jx0) * jzl + (bz + a - jz0), v);
-                    } else {
-                        const int gz = bz + a;
-                        if ((unsigned)gz < (unsigned)g.nz) atomicAdd(J + c * N + wrapi(bx + b, g.nx) * g.nz + gz, v);
-                    }
+                // only live lanes own a window inside the box (dead or empty slots are one-lane
+                // runs with no window; their sums are zero and they must not write)
+                if (jtile) {
+                    if (seg.head && ok && v != 0.f) atomicAdd(sJ + c * jvol + sbase + b * jzl + a, v);
+                } else {
+                    const int gz = bz + a;
+                    if (seg.head && ok && v != 0.f && (unsigned)gz < (unsigned)g.nz)
+                        atomicAdd(J + c * N + grow[b] + gz, v);
                 }
             };
 #pragma unroll
@@ -958,13 +979,22 @@ __global__ void add_count_kernel(int32_t* count, long long nnew, long long cap) 
     if (*count + nnew <= cap) *count += (int32_t)nnew;
 }
 
-// ---- counting sort by cell ----
-__global__ void hist_kernel(SpeciesP sp, int32_t* hist) {
+// ---- counting sort by 8 x 8-cell tiles of (z, x), cells in each tile z-fastest ----
+// (a chunk of consecutive particles then covers a compact patch, which keeps the shared-memory
+// boxes of the fused kernels small)
+__device__ __forceinline__ int sort_key(const GridP& g, int cell) {
+    int izg, ix, iy;
+    decode(g, cell, izg, ix, iy);
+    const int ntz = (g.nzg + 7) >> 3, ntx = (g.nx + 7) >> 3;
+    return ((iy * ntx + (ix >> 3)) * ntz + (izg >> 3)) * 64 + ((ix & 7) << 3) + (izg & 7);
+}
+
+__global__ void hist_kernel(GridP g, SpeciesP sp, int32_t* hist) {
     const long long n = *sp.count;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         int c = sp.cell[p];
-        if (c >= 0) atomicAdd(hist + c, 1);
+        if (c >= 0) atomicAdd(hist + sort_key(g, c), 1);
     }
 }
 
@@ -1043,7 +1073,7 @@ __global__ void add_block_offsets_kernel(int32_t* a, long long n, const int32_t*
 }
 
 template <int NDIM>
-__global__ void scatter_kernel(SpeciesP sp, int32_t* cursor, int32_t* cell2, float* off2, float* u2,
+__global__ void scatter_kernel(GridP g, SpeciesP sp, int32_t* cursor, int32_t* cell2, float* off2, float* u2,
                                int32_t* id2) {
     const long long n = *sp.count;
     const long long cap = sp.cap;
@@ -1051,7 +1081,7 @@ __global__ void scatter_kernel(SpeciesP sp, int32_t* cursor, int32_t* cell2, flo
          p += (long long)gridDim.x * blockDim.x) {
         int c = sp.cell[p];
         if (c < 0) continue;
-        long long d = atomicAdd(cursor + c, 1);
+        long long d = atomicAdd(cursor + sort_key(g, c), 1);
         cell2[d] = c;
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) off2[k * cap + d] = sp.off[k * cap + p];
@@ -1234,23 +1264,28 @@ cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], 
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const GridP& g, const SpeciesP& sp, long long extent, int32_t* hist,
+long long sort_bins(const GridP& g) {
+    return (long long)g.ny * ((g.nx + 7) / 8) * ((g.nzg + 7) / 8) * 64;
+}
+
+cudaError_t launch_sort(const GridP& g0, const SpeciesP& sp, long long extent, int32_t* hist,
                         int32_t* blocksums, int32_t* cell_alt, float* off_alt, float* u_alt,
                         int32_t* id_alt, cudaStream_t s) {
     if (extent <= 0) return cudaSuccess;
-    const long long nb = (long long)g.nzg * g.nx * g.ny;
+    const GridP g = prep(g0);
+    const long long nb = sort_bins(g);
     cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int32_t) * nb, s);
     if (e != cudaSuccess) return e;
-    hist_kernel<<<pblocks(extent), 256, 0, s>>>(sp, hist);
+    hist_kernel<<<pblocks(extent), 256, 0, s>>>(g, sp, hist);
     long long nblk = (nb + SCAN_B - 1) / SCAN_B;
     scan_blocks_kernel<<<(unsigned)nblk, SCAN_T, 0, s>>>(hist, nb, blocksums);
     scan_sums_kernel<<<1, SCAN_T, 0, s>>>(blocksums, nblk);
     add_block_offsets_kernel<<<nblocks(nb, 256), 256, 0, s>>>(hist, nb, blocksums);
     if (g.ndim == 2)
-        scatter_kernel<2><<<pblocks(extent), 256, 0, s>>>(sp, hist, cell_alt, off_alt, u_alt,
+        scatter_kernel<2><<<pblocks(extent), 256, 0, s>>>(g, sp, hist, cell_alt, off_alt, u_alt,
                                                                sp.id ? id_alt : nullptr);
     else
-        scatter_kernel<3><<<pblocks(extent), 256, 0, s>>>(sp, hist, cell_alt, off_alt, u_alt,
+        scatter_kernel<3><<<pblocks(extent), 256, 0, s>>>(g, sp, hist, cell_alt, off_alt, u_alt,
                                                                sp.id ? id_alt : nullptr);
     if (g.ndim == 2)
         copy_back_kernel<2><<<pblocks(extent), 256, 0, s>>>(sp, blocksums + nblk, cell_alt, off_alt, u_alt,

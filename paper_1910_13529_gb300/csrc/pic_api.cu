@@ -64,6 +64,7 @@ struct pic_t {
     std::vector<int> ev_cat;
     size_t ev_used = 0;
     long long launches[PIC_TIMING_N] = {0};
+    float* adj_scratch = nullptr; // adjoint: B', E', W (7 N floats)
     int fa_variant = 0;           // field-advance tile variant (pic_autotune)
     double fa_ms[8] = {0};        // measured time per variant (ms), 0 = not measured
 };
@@ -228,7 +229,7 @@ pic_status ensure_sort_scratch(pic_t* h) {
             ids = ids || q.id;
         }
     if (!h->hist) {
-        long long nb = (long long)h->g.nzg * h->g.nx * h->g.ny;
+        long long nb = sort_bins(h->g);
         pic_status st = dalloc(h, &h->hist, nb, "sort histogram");
         if (st) return st;
         if ((st = dalloc(h, &h->blocksums, nb / 4096 + 16, "sort block sums"))) return st;
@@ -382,6 +383,7 @@ pic_status pic_destroy(pic_t* h) {
     void* ptrs[] = {h->E2, h->B2, h->rho64, h->acc, h->status, h->counts, h->hist, h->blocksums,
                     h->cell_alt, h->off_alt, h->u_alt, h->id_alt};
     for (void* p : ptrs) dfree(p);
+    dfree(h->adj_scratch);
     for (size_t i = 0; i < h->ev_a.size(); ++i) {
         cudaEventDestroy(h->ev_a[i]);
         cudaEventDestroy(h->ev_b[i]);
@@ -655,6 +657,22 @@ pic_status pic_get_state(const pic_t* h, int64_t* step, int64_t* shifts, int* pe
     return PIC_OK;
 }
 
+pic_status pic_set_state(pic_t* h, int64_t step, int64_t shifts, int pending_shift, int64_t next_id) {
+    if (!h || step < 0 || shifts < 0 || next_id < 0 || (pending_shift != 0 && pending_shift != 1)) return PIC_ERR_ARG;
+    if (h->state == 1) return fail(h, PIC_ERR_STATE, "pic_set_state between pic_gather_push and pic_deposit");
+    h->step = step;
+    h->shifts = shifts;
+    h->pending_shift = pending_shift;
+    h->next_id = next_id;
+    return PIC_OK;
+}
+
+pic_status pic_get_next_id(const pic_t* h, int64_t* next_id) {
+    if (!h || !next_id) return PIC_ERR_ARG;
+    *next_id = h->next_id;
+    return PIC_OK;
+}
+
 pic_status pic_sync(pic_t* h, void* stream) {
     if (!h) return PIC_ERR_ARG;
     CK(h, cudaStreamSynchronize((cudaStream_t)stream), "synchronise");
@@ -687,6 +705,37 @@ pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream
         if (ms) ms[c] = acc[c];
         if (launches) launches[c] = h->launches[c];
     }
+    return PIC_OK;
+}
+
+pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const float* J, float* aE, float* aB,
+                            double* grad, void* stream) {
+    if (!h || !E || !B || !J || !aE || !aB || !grad) return PIC_ERR_ARG;
+    const long long N = h->g.ncell;
+    if (!h->adj_scratch) {
+        pic_status st = dalloc(h, &h->adj_scratch, 7 * N, "adjoint scratch");
+        if (st) return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* Bh = h->adj_scratch;        // B' = B - h T E
+    float* Ep = Bh + 3 * N;            // E' = E + dt (S B' - J)
+    float* W = Ep + 3 * N;             // P^{-1} aE1
+    const float dt = h->g.dt, hh = 0.5f * dt;
+    const int M = h->st.M;
+    const GridP& g = h->g;
+    CK(h, launch_curl_plus_update(g, h->st, B, E, -hh, Bh, s), "adjoint: B half step");
+    CK(h, launch_curl_minus_update(g, h->st, E, Bh, J, dt, -dt, Ep, s), "adjoint: E step");
+    CK(h, launch_grad_plus(g, M, aB, Ep, -(double)hh, grad, s), "adjoint: gradient (third stage)");
+    CK(h, launch_curl_minus_update(g, h->st, aE, aB, nullptr, -hh, 0.f, aE, s), "adjoint: third stage");
+    CK(h, launch_grad_minus(g, M, aE, Bh, (double)dt, grad, s), "adjoint: gradient (second stage)");
+    if (h->hlen > 0) {
+        CK(h, cudaMemcpyAsync(W, aE, sizeof(float) * N, cudaMemcpyDeviceToDevice, s), "adjoint: copy aE1");
+        CK(h, launch_correct_j1(g, h->hf, h->hlen, W, s), "adjoint: P^-1 aE1");
+        CK(h, launch_grad_corr(g, M, W, J, (double)dt, grad, s), "adjoint: gradient (correction)");
+    }
+    CK(h, launch_curl_plus_update(g, h->st, aB, aE, dt, aB, s), "adjoint: second stage");
+    CK(h, launch_grad_plus(g, M, aB, E, -(double)hh, grad, s), "adjoint: gradient (first stage)");
+    CK(h, launch_curl_minus_update(g, h->st, aE, aB, nullptr, -hh, 0.f, aE, s), "adjoint: first stage");
     return PIC_OK;
 }
 
@@ -748,6 +797,13 @@ pic_status pic_autotune(pic_t* h, void* stream) {
     cudaEventDestroy(b);
     h->fa_variant = best;
     cache.push_back({key, best});
+    return PIC_OK;
+}
+
+pic_status pic_set_tuning(pic_t* h, int variant) {
+    if (!h) return PIC_ERR_ARG;
+    if (variant < 0 || variant >= field_variants(h->g.ndim)) return fail(h, PIC_ERR_ARG, "tile variant %d", variant);
+    h->fa_variant = variant;
     return PIC_OK;
 }
 

@@ -111,6 +111,7 @@ cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J,
                                    cudaStream_t s);
 cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], long long next_id,
                           int* status, cudaStream_t s);
+long long sort_bins(const GridP& g);
 cudaError_t launch_sort(const GridP& g, const SpeciesP& sp, long long extent, int32_t* hist,
                         int32_t* blocksums, int32_t* cell_alt, float* off_alt, float* u_alt,
                         int32_t* id_alt, cudaStream_t s);
@@ -123,6 +124,18 @@ cudaError_t launch_diag_reduce(const GridP& g, const StencilP& st, const float* 
                                cudaStream_t s);
 cudaError_t launch_kinetic(const GridP& g, const SpeciesP& sp, long long extent, double* acc,
                            cudaStream_t s);
+
+// ---- adjoint (adjoint_kernels.cu) ----
+cudaError_t launch_curl_plus_update(const GridP& g, const StencilP& st, const float* X, const float* Y, float a,
+                                    float* out, cudaStream_t s);
+cudaError_t launch_curl_minus_update(const GridP& g, const StencilP& st, const float* X, const float* Y, const float* J,
+                                     float a, float b, float* out, cudaStream_t s);
+cudaError_t launch_grad_plus(const GridP& g, int M, const float* L, const float* F, double a, double* grad,
+                             cudaStream_t s);
+cudaError_t launch_grad_minus(const GridP& g, int M, const float* L, const float* F, double a, double* grad,
+                              cudaStream_t s);
+cudaError_t launch_grad_corr(const GridP& g, int M, const float* W, const float* J1c, double a, double* grad,
+                             cudaStream_t s);
 
 // ---- host math (host_math.cpp) ----
 int fit_coefficients(double kappa, int M, double wk, double n, double* C);

@@ -8,8 +8,8 @@ import torch
 from . import (PIC_SOLVER_CUSTOM, PIC_SOLVER_YEE, encode_cells, pic_batch_create, pic_batch_destroy,
                pic_batch_instance, pic_batch_step, pic_bind_fields, pic_bind_species,
                pic_config, pic_create, pic_deposit, pic_destroy, pic_diag, pic_field_advance,
-               pic_gather_push, pic_gauss, pic_get_coefficients, pic_get_count, pic_get_state, pic_rho,
-               pic_sort, pic_step, pic_sync)
+               pic_autotune, pic_gather_push, pic_gauss, pic_get_coefficients, pic_get_count, pic_get_state,
+               pic_get_tuning, pic_rho, pic_sort, pic_step, pic_sync)
 
 
 def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee", M=16, coef=None,
@@ -97,6 +97,11 @@ class Simulation:
     def sort(self):
         pic_sort(self.h, self.stream)
 
+    def autotune(self):
+        """Pick the fastest field-advance tile shape for this grid (pic_autotune)."""
+        pic_autotune(self.h, self.stream)
+        return pic_get_tuning(self.h)
+
     # ---- diagnostics ----
     def diag(self):
         return pic_diag(self.h, self.stream)
@@ -122,6 +127,30 @@ class Simulation:
 
     def sync(self):
         pic_sync(self.h, self.stream)
+
+    def save(self, path):
+        """Checkpoint: fields, particle arrays and the run counters, to a host file."""
+        from . import pic_get_next_id
+        step, shifts, pending = self.state()
+        sp = {s: {k: (v.cpu() if torch.is_tensor(v) else v) for k, v in d.items()} | {"n": self.count(s)}
+              for s, d in self.species.items()}
+        torch.save({"E": self.E.cpu(), "B": self.B.cpu(), "J": self.J.cpu(), "species": sp, "step": step,
+                    "shifts": shifts, "pending": pending, "next_id": pic_get_next_id(self.h)}, path)
+
+    def load(self, path):
+        """Resume from save(): same configuration, arrays and counters restored."""
+        from . import pic_set_state
+        d = torch.load(path, weights_only=False)
+        self.E.copy_(d["E"])
+        self.B.copy_(d["B"])
+        self.J.copy_(d["J"])
+        for s, q in d["species"].items():
+            dev = {k: (v.to(self.device) if torch.is_tensor(v) else v) for k, v in q.items()}
+            self.species[s] = {k: dev[k] for k in ("cell", "off", "u", "id", "q", "m", "w", "cap")}
+            pic_bind_species(self.h, s, dev["cell"].data_ptr(), dev["off"].data_ptr(), dev["u"].data_ptr(),
+                             dev["id"].data_ptr() if dev["id"] is not None else None, q["n"], q["cap"], q["q"],
+                             q["m"], q["w"])
+        pic_set_state(self.h, d["step"], d["shifts"], d["pending"], d["next_id"])
 
     def particles(self, s):
         """Host copy of slots [0, count) of species s: cell, off (ndim, n), u (3, n), id."""
@@ -175,3 +204,103 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class StencilLoss:
+    """Field energy left behind a rigidly moving beam after `nsteps`, as a function of the axial
+    stencil coefficients C, with its gradient from the hand-written adjoint (pic_adjoint_step).
+
+    The particles are held rigid (their momenta never change) by giving them an effectively
+    infinite mass; the loss is (1/2) sum (E^2 + B^2) dV over the cells with z index below
+    (beam z index - behind).  The forward pass keeps a checkpoint (fields and particles) every
+    `every` steps; the backward pass replays each segment from its checkpoint, keeping the fields
+    and currents of every step of the segment, and runs the adjoint steps in reverse."""
+
+    RIGID_MASS = 1e30
+
+    def __init__(self, grid, species, nsteps, every=50, behind=2, device="cuda:0"):
+        self.grid = dict(grid)
+        self.species = species
+        self.nsteps, self.every, self.behind = int(nsteps), int(every), int(behind)
+        self.device = torch.device(device)
+
+    def _sim(self, C):
+        kw = {k: self.grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape") if k in self.grid}
+        sim = Simulation(device=str(self.device), solver="custom", coef=np.asarray(C, dtype=np.float64), **kw)
+        for s, sp in enumerate(self.species):
+            sim.add_species(s, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], self.RIGID_MASS, sp["w"])
+        return sim
+
+    def _mask_z(self, sim):
+        """z index below which the loss is taken: the beam's lowest cell minus `behind`."""
+        zmin = None
+        for s in sim.species:
+            cell = sim.species[s]["cell"][: sim.count(s)].cpu().numpy()
+            iz = cell[cell >= 0] % (sim.nz + 2) - 1
+            zmin = int(iz.min()) if zmin is None else min(zmin, int(iz.min()))
+        return max(zmin - self.behind, 0)
+
+    def _loss(self, sim, zc):
+        dV = sim.cfg["dz"] * sim.cfg["dx"] * (sim.cfg.get("dy", 1.0) if sim.ndim == 3 else 1.0)
+        E = sim.E[..., :zc].double()
+        B = sim.B[..., :zc].double()
+        return 0.5 * float((E ** 2).sum() + (B ** 2).sum()) * dV, dV
+
+    def loss(self, C):
+        sim = self._sim(C)
+        sim.step(self.nsteps)
+        L, _ = self._loss(sim, self._mask_z(sim))
+        sim.close()
+        return L
+
+    def loss_and_grad(self, C):
+        from . import pic_adjoint_step
+        sim = self._sim(C)
+        ckpt = []
+        for n in range(self.nsteps):
+            if n % self.every == 0:
+                ckpt.append((n, sim.E.clone(), sim.B.clone(),
+                             {s: {k: sim.species[s][k].clone() for k in ("cell", "off", "u")} for s in sim.species}))
+            sim.step(1)
+        zc = self._mask_z(sim)
+        L, dV = self._loss(sim, zc)
+        aE = torch.zeros_like(sim.E)
+        aB = torch.zeros_like(sim.B)
+        aE[..., :zc] = sim.E[..., :zc] * dV
+        aB[..., :zc] = sim.B[..., :zc] * dV
+        grad = torch.zeros(len(C), dtype=torch.float64, device=self.device)
+        stream = sim.stream
+        for n0, E0, B0, parts in reversed(ckpt):
+            n1 = min(n0 + self.every, self.nsteps)
+            sim.E.copy_(E0)
+            sim.B.copy_(B0)
+            for s, arrs in parts.items():
+                for k, v in arrs.items():
+                    sim.species[s][k].copy_(v)
+            saved = []
+            for _ in range(n0, n1):
+                En, Bn = sim.E.clone(), sim.B.clone()
+                sim.step(1)
+                saved.append((En, Bn, sim.J.clone()))
+            for En, Bn, Jn in reversed(saved):
+                pic_adjoint_step(sim.h, En.data_ptr(), Bn.data_ptr(), Jn.data_ptr(), aE.data_ptr(), aB.data_ptr(),
+                                 grad.data_ptr(), stream)
+        torch.cuda.synchronize(self.device)
+        g = grad.cpu().numpy()
+        sim.close()
+        return L, g
+
+
+class StencilLossFn(torch.autograd.Function):
+    """torch.autograd wrapper: loss = StencilLossFn.apply(C, problem) with C a CPU float64 tensor."""
+
+    @staticmethod
+    def forward(ctx, C, problem):
+        L, g = problem.loss_and_grad(C.detach().cpu().numpy())
+        ctx.save_for_backward(torch.from_numpy(g))
+        return torch.tensor(L, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gL):
+        (g,) = ctx.saved_tensors
+        return gL * g, None

@@ -37,3 +37,26 @@ def test_yee_on_axis_e1_matches_kspace_integral():
     assert np.max(np.abs(sim_v - ref)) < band
     # the Cerenkov wake lies behind the particle (Sec. 2.2)
     assert np.max(np.abs(E1[N - 40:N - 10])) > 20 * np.max(np.abs(E1[N + 10:N + 30]))
+
+
+def test_customised_solver_removes_the_cerenkov_wake():
+    """Sec. 3: with [k]_1 ~ [k1]_t there is no Cerenkov-like field from the fundamental zone, so
+    the oscillating field behind a beta -> 1 particle is several times weaker than with Yee.
+    The uniform part behind the particle (the same for both solvers: the periodic transverse
+    box) is removed by comparing the spread about the mean over i' in [-150, -20]."""
+    from oracle import fit
+    C = np.loadtxt(__file__.replace("test_oracle_single_particle.py", "golden/table1_coefficients.txt"))
+    nz, nx = 240, 64
+    spread, mean = {}, {}
+    for solver in ("yee", "custom"):
+        g = oc.Grid(2, nz, nx, 1, 1.0, 1.0, 1.0, 0.25, C=(C if solver == "custom" else (1.0,)), shape=1)
+        sim = oc.Sim(g, [oc.Species(np.array([[nz - 30.0, nx // 2, 0.0]]), np.array([[1e7, 0.0, 0.0]]), 1.0, 1.0,
+                                    1.0)], h=(fit.correction_kernel(C, 40) if solver == "custom" else None),
+                     moving_window=True)
+        for _ in range(1000):
+            sim.step()
+        N = int(round(sim.species[0].xi[0, 0]))
+        seg = sim.E[0, 0, nx // 2, N - 150:N - 20]
+        spread[solver], mean[solver] = seg.std(), seg.mean()
+    assert spread["custom"] < 0.35 * spread["yee"]
+    assert abs(mean["custom"] - mean["yee"]) < 0.1 * abs(mean["yee"])
