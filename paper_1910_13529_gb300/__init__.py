@@ -249,7 +249,7 @@ def pic_autotune(h, stream):
 
 def pic_get_tuning(h):
     v, nv = ctypes.c_int(), ctypes.c_int()
-    ms = np.zeros(8)
+    ms = np.zeros(16)
     _check(lib.pic_get_tuning(h, ctypes.byref(v), _dptr(ms), ctypes.byref(nv)), h)
     return v.value, ms[: nv.value]
 

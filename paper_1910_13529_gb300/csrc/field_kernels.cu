@@ -13,6 +13,8 @@
 // buffer lets the moving-window shift be folded into the store.
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 #include "pic_internal.h"
 
 namespace pic {
@@ -219,6 +221,308 @@ __device__ __forceinline__ void advance_tile(const FieldP& p, int tz, int tx, in
     }
 }
 
+// ---- register-blocked tile ---------------------------------------------------------------
+// Same three stages, but every thread produces four consecutive z cells of a stage.  The axial
+// derivative of those four cells needs 2 MP + 3 consecutive values of the differentiated
+// component (MP = MAXM rounded up to 4); the thread reads them as MP / 2 + 1 aligned 128-bit
+// shared loads into registers instead of 2 MAXM scalar loads per cell, which cuts the shared-
+// memory traffic of the M = 16 stencil about four-fold.  Every halo is a multiple of 4 cells
+// and all component rows start on a 16-byte boundary, so with the E windows starting one cell
+// below the d+ stencil and the B windows exactly at the d- stencil, every window, every
+// same-cell read and every store of the three stages is aligned:
+//   B^{n+1/2} on z in [-2 MP, TZ + 2 MP), E^{n+1} on [-MP, TZ + MP), B^{n+1} on [0, TZ),
+//   E^n staged on [-3 MP, TZ + 3 MP).
+// E^n, B^n and J of the tile are all staged before the first stage (16-byte cp.async copies
+// when nz % 4 == 0, so the CTA's global reads are in flight together); B^{n+1/2} overwrites
+// B^n in place and E^{n+1} overwrites E^n.
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+struct TileRB {
+    static constexpr int MP = (MAXM + 3) & ~3;
+    static constexpr int H2 = MP, H1 = 2 * MP, H0 = 3 * MP;
+    static constexpr int WE = TZ + 2 * H0;            // E row length (floats)
+    static constexpr int WB = TZ + 2 * H1;            // B row length
+    static constexpr int WJ = TZ + 2 * H2;            // J row length
+    static constexpr int TYe = NDIM == 3 ? TY : 1;
+    static constexpr int RX0 = TX + 3, RY0 = NDIM == 3 ? TY + 3 : 1;   // E rows: [-1, T+1]
+    static constexpr int RX1 = TX + 2, RY1 = NDIM == 3 ? TY + 2 : 1;   // B rows: [-1, T]
+    static constexpr int RX2 = TX + 1, RY2 = NDIM == 3 ? TY + 1 : 1;   // E', J rows: [0, T]
+    static constexpr int SE = RX0 * RY0 * WE;
+    static constexpr int SB = RX1 * RY1 * WB;
+    static constexpr int SJ = RX2 * RY2 * WJ;
+    static constexpr size_t smem_bytes = sizeof(float) * 3 * (SE + SB + SJ);
+    static_assert(TZ % 4 == 0, "the z tile holds whole groups of four cells");
+};
+
+__device__ __forceinline__ void lds4(float (&a)[4], const float* s) {
+    const float4 v = *reinterpret_cast<const float4*>(s);
+    a[0] = v.x;
+    a[1] = v.y;
+    a[2] = v.z;
+    a[3] = v.w;
+}
+
+__device__ __forceinline__ void sts4(float* s, const float (&a)[4]) {
+    *reinterpret_cast<float4*>(s) = make_float4(a[0], a[1], a[2], a[3]);
+}
+
+// 16-byte asynchronous global -> shared copy; valid == false writes zeros (nothing is read,
+// src must still be a mapped address).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
+}
+
+// Rows of a staged field: `rows` rows of `w` floats (w % 4 == 0) covering z in [zlo, zlo + w)
+// of global rows (x0 + rx + dxy, y0 + ry + dxy) (periodic in x, y), components f0, f1, f2
+// into dst[c * cstride + r * w + col]; zero outside 0 <= z < nz.
+template <int NDIM, int RX>
+__device__ __forceinline__ void stage_rows(float* dst, int cstride, const float* __restrict__ f0,
+                                           const float* __restrict__ f1, const float* __restrict__ f2, int rows,
+                                           int w, int zlo, int x0, int y0, int dxy, const GridP& g, bool vec) {
+    const float* f[3] = {f0, f1, f2};
+    const int ng = w >> 2;
+    for (int it = threadIdx.x; it < rows * ng; it += blockDim.x) {
+        const int gi = it % ng, r = it / ng;
+        const int rx = r % RX, ry = r / RX;
+        const int gz = zlo + 4 * gi;
+        const int gx = wrapi(x0 + rx + dxy, g.nx);
+        const int gy = NDIM == 3 ? wrapi(y0 + ry + dxy, g.ny) : 0;
+        const long long row = ((long long)gy * g.nx + gx) * g.nz;
+        float* d = dst + r * w + 4 * gi;
+        if (vec) {
+            const bool in = gz >= 0 && gz < g.nz;
+            const long long o = in ? row + gz : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cp_async16(d + c * cstride, f[c] + o, in);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float a[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    a[j] = (gz + j >= 0 && gz + j < g.nz) ? __ldg(f[c] + row + gz + j) : 0.f;
+                sts4(d + c * cstride, a);
+            }
+        }
+    }
+}
+
+// w[k] = f[z - MP + k], k < 2 MP + 4, from the aligned window at s.
+//   d+ (E -> B, Appendix C):  d[j] = sum_l C_l (f[z+j+l] - f[z+j-l+1]),  l = 1..M
+//   d- (B -> E):              d[j] = sum_l C_l (f[z+j+l-1] - f[z+j-l])
+// mid[j] = f[z+j].  Coefficients beyond M are zero.
+template <int MAXM, int MP, bool PLUS>
+__device__ __forceinline__ void window_dz(const StencilP& st, const float* s, float (&d)[4], float (&mid)[4]) {
+    constexpr int NW = 2 * MP + 4;
+    float w[NW];
+#pragma unroll
+    for (int q = 0; q < NW / 4; ++q) {
+        float a[4];
+        lds4(a, s + 4 * q);
+        w[4 * q] = a[0];
+        w[4 * q + 1] = a[1];
+        w[4 * q + 2] = a[2];
+        w[4 * q + 3] = a[3];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float acc = 0.f;
+#pragma unroll
+        for (int l = 1; l <= MAXM; ++l) {
+            const float df = PLUS ? w[MP + j + l] - w[MP + j - l + 1] : w[MP + j + l - 1] - w[MP + j - l];
+            acc = fmaf(st.C[l - 1], df, acc);
+        }
+        d[j] = acc;
+        mid[j] = w[MP + j];
+    }
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+__device__ __forceinline__ void advance_tile_rb(const FieldP& p, int tz, int tx, int ty, float* smem) {
+    using T = TileRB<NDIM, MAXM, TZ, TX, TY>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, WJ = T::WJ;
+    float* sE = smem;                             // [3][RY0][RX0][WE]
+    float* sB = smem + 3 * T::SE;                 // [3][RY1][RX1][WB]
+    float* sJ = smem + 3 * (T::SE + T::SB);       // [3][RY2][RX2][WJ]
+
+    const GridP& g = p.g;
+    const int nz = g.nz, nx = g.nx, ny = g.ny;
+    const long long N = g.ncell;
+    const int z0 = tz * TZ, x0 = tx * TX, y0 = NDIM == 3 ? ty * TY : 0;
+    const bool vec = p.vec4 != 0;
+    const float dt = g.dt;
+    const float hz = 0.5f * dt / g.dz, fz = dt / g.dz;
+    const float hx = 0.5f * dt / g.dx, fx = dt / g.dx;
+    const float hy = NDIM == 3 ? 0.5f * dt / g.dy : 0.f, fy = NDIM == 3 ? dt / g.dy : 0.f;
+
+    // ---- stage 0: E^n (rows from -1), B^n (rows from -1), J (rows from 0) ------------------
+    stage_rows<NDIM, T::RX0>(sE, T::SE, p.Ein, p.Ein + N, p.Ein + 2 * N, T::RY0 * T::RX0, WE, z0 - T::H0, x0, y0,
+                             -1, g, vec);
+    stage_rows<NDIM, T::RX1>(sB, T::SB, p.Bin, p.Bin + N, p.Bin + 2 * N, T::RY1 * T::RX1, WB, z0 - T::H1, x0, y0,
+                             -1, g, vec);
+    stage_rows<NDIM, T::RX2>(sJ, T::SJ, p.J1, p.J2, p.J3, T::RY2 * T::RX2, WJ, z0 - T::H2, x0, y0, 0, g, vec);
+    if (vec) cp_async_wait_all();
+    __syncthreads();
+
+    // ---- stage 1: B^{n+1/2} in place, rows x in [-1, TX] (y in [-1, TY]), z in [-H1, TZ+H1) --
+    constexpr int NG1 = WB / 4;
+    for (int it = threadIdx.x; it < T::RY1 * T::RX1 * NG1; it += blockDim.x) {
+        const int gi = it % NG1, r = it / NG1;
+        const int rx = r % T::RX1, ry = r / T::RX1;
+        const int z = 4 * gi - T::H1;
+        const int gz = z0 + z;
+        if (gz + 3 < 0 || gz >= nz) continue;                       // B^n = B^{n+1/2} = 0 there
+        const int e = (ry * T::RX0 + rx) * WE + z + T::H0;          // E rows also start at -1
+        float d2[4], d3[4], e2[4], e3[4], e1[4], e1x[4], e3x[4];
+        float e1y[4] = {0.f, 0.f, 0.f, 0.f}, e2y[4] = {0.f, 0.f, 0.f, 0.f};
+        window_dz<MAXM, MP, true>(p.st, sE + T::SE + e - MP, d2, e2);
+        window_dz<MAXM, MP, true>(p.st, sE + 2 * T::SE + e - MP, d3, e3);
+        lds4(e1, sE + e);
+        lds4(e1x, sE + e + WE);
+        lds4(e3x, sE + 2 * T::SE + e + WE);
+        if (NDIM == 3) {
+            lds4(e1y, sE + e + T::RX0 * WE);
+            lds4(e2y, sE + T::SE + e + T::RX0 * WE);
+        }
+        const int cb = r * WB + 4 * gi;
+        float b0[4], b1[4], b2[4];
+        lds4(b0, sB + cb);
+        lds4(b1, sB + T::SB + cb);
+        lds4(b2, sB + 2 * T::SB + cb);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = gz + j >= 0 && gz + j < nz;
+            b0[j] = in ? b0[j] - (hx * (e3x[j] - e3[j]) - hy * (e2y[j] - e2[j])) : 0.f;
+            b1[j] = in ? b1[j] - (hy * (e1y[j] - e1[j]) - hz * d3[j]) : 0.f;
+            b2[j] = in ? b2[j] - (hz * d2[j] - hx * (e1x[j] - e1[j])) : 0.f;
+        }
+        sts4(sB + cb, b0);
+        sts4(sB + T::SB + cb, b1);
+        sts4(sB + 2 * T::SB + cb, b2);
+    }
+    __syncthreads();
+
+    // ---- stage 2: E^{n+1} in place, rows x in [0, TX] (y in [0, TY]), z in [-H2, TZ+H2) ------
+    constexpr int NG2 = WJ / 4;
+    for (int it = threadIdx.x; it < T::RY2 * T::RX2 * NG2; it += blockDim.x) {
+        const int gi = it % NG2, r = it / NG2;
+        const int rx = r % T::RX2, ry = r / T::RX2;
+        const int z = 4 * gi - T::H2;
+        const int gz = z0 + z;
+        if (gz + 3 < 0 || gz >= nz) continue;                       // E^n = E^{n+1} = 0 there
+        const int e = ((NDIM == 3 ? (ry + 1) * T::RX0 : 0) + rx + 1) * WE + z + T::H0;
+        const int b = ((NDIM == 3 ? (ry + 1) * T::RX1 : 0) + rx + 1) * WB + z + T::H1;
+        float d2[4], d3[4], B2[4], B3[4], B1[4], B1x[4], B3x[4];
+        float B1y[4] = {0.f, 0.f, 0.f, 0.f}, B2y[4] = {0.f, 0.f, 0.f, 0.f};
+        window_dz<MAXM, MP, false>(p.st, sB + T::SB + b - MP, d2, B2);
+        window_dz<MAXM, MP, false>(p.st, sB + 2 * T::SB + b - MP, d3, B3);
+        lds4(B1, sB + b);
+        lds4(B1x, sB + b - WB);
+        lds4(B3x, sB + 2 * T::SB + b - WB);
+        if (NDIM == 3) {
+            lds4(B1y, sB + b - T::RX1 * WB);
+            lds4(B2y, sB + T::SB + b - T::RX1 * WB);
+        }
+        const int cj = r * WJ + 4 * gi;
+        float e0[4], e1[4], e2[4], j0[4], j1[4], j2[4];
+        lds4(e0, sE + e);
+        lds4(e1, sE + T::SE + e);
+        lds4(e2, sE + 2 * T::SE + e);
+        lds4(j0, sJ + cj);
+        lds4(j1, sJ + T::SJ + cj);
+        lds4(j2, sJ + 2 * T::SJ + cj);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = gz + j >= 0 && gz + j < nz;
+            e0[j] = in ? e0[j] + (fx * (B3[j] - B3x[j]) - fy * (B2[j] - B2y[j])) - dt * j0[j] : 0.f;
+            e1[j] = in ? e1[j] + (fy * (B1[j] - B1y[j]) - fz * d3[j]) - dt * j1[j] : 0.f;
+            e2[j] = in ? e2[j] + (fz * d2[j] - fx * (B1[j] - B1x[j])) - dt * j2[j] : 0.f;
+        }
+        sts4(sE + e, e0);
+        sts4(sE + T::SE + e, e1);
+        sts4(sE + 2 * T::SE + e, e2);
+    }
+    __syncthreads();
+
+    // ---- stage 3: B^{n+1} on the tile; store E^{n+1}, B^{n+1} (shifted if the window moves) --
+    constexpr int NG3 = TZ / 4;
+    for (int it = threadIdx.x; it < T::TYe * TX * NG3; it += blockDim.x) {
+        const int gi = it % NG3, r = it / NG3;
+        const int x = r % TX, y = r / TX;
+        const int z = 4 * gi;
+        const int gz = z0 + z, gx = x0 + x, gy = y0 + y;
+        if (gz >= nz || gx >= nx || (NDIM == 3 && gy >= ny)) continue;
+        const int e = ((NDIM == 3 ? (y + 1) * T::RX0 : 0) + x + 1) * WE + z + T::H0;
+        const int b = ((NDIM == 3 ? (y + 1) * T::RX1 : 0) + x + 1) * WB + z + T::H1;
+        float d2[4], d3[4], e2[4], e3[4], e1[4], e1x[4], e3x[4];
+        float e1y[4] = {0.f, 0.f, 0.f, 0.f}, e2y[4] = {0.f, 0.f, 0.f, 0.f};
+        window_dz<MAXM, MP, true>(p.st, sE + T::SE + e - MP, d2, e2);
+        window_dz<MAXM, MP, true>(p.st, sE + 2 * T::SE + e - MP, d3, e3);
+        lds4(e1, sE + e);
+        lds4(e1x, sE + e + WE);
+        lds4(e3x, sE + 2 * T::SE + e + WE);
+        if (NDIM == 3) {
+            lds4(e1y, sE + e + T::RX0 * WE);
+            lds4(e2y, sE + T::SE + e + T::RX0 * WE);
+        }
+        float b0[4], b1[4], b2[4];
+        lds4(b0, sB + b);
+        lds4(b1, sB + T::SB + b);
+        lds4(b2, sB + 2 * T::SB + b);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            b0[j] -= hx * (e3x[j] - e3[j]) - hy * (e2y[j] - e2[j]);
+            b1[j] -= hy * (e1y[j] - e1[j]) - hz * d3[j];
+            b2[j] -= hz * d2[j] - hx * (e1x[j] - e1[j]);
+        }
+        const long long row = ((long long)gy * nx + gx) * nz;
+        if (vec && !p.shift) {
+            const long long o = row + gz;
+            *reinterpret_cast<float4*>(p.Eout + o) = make_float4(e1[0], e1[1], e1[2], e1[3]);
+            *reinterpret_cast<float4*>(p.Eout + N + o) = make_float4(e2[0], e2[1], e2[2], e2[3]);
+            *reinterpret_cast<float4*>(p.Eout + 2 * N + o) = make_float4(e3[0], e3[1], e3[2], e3[3]);
+            *reinterpret_cast<float4*>(p.Bout + o) = make_float4(b0[0], b0[1], b0[2], b0[3]);
+            *reinterpret_cast<float4*>(p.Bout + N + o) = make_float4(b1[0], b1[1], b1[2], b1[3]);
+            *reinterpret_cast<float4*>(p.Bout + 2 * N + o) = make_float4(b2[0], b2[1], b2[2], b2[3]);
+            continue;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gzj = gz + j;
+            if (gzj >= nz) break;
+            const int oz = gzj - p.shift;
+            if (oz >= 0) {
+                const long long o = row + oz;
+                p.Eout[o] = e1[j];
+                p.Eout[N + o] = e2[j];
+                p.Eout[2 * N + o] = e3[j];
+                p.Bout[o] = b0[j];
+                p.Bout[N + o] = b1[j];
+                p.Bout[2 * N + o] = b2[j];
+            }
+            if (p.shift && gzj == nz - 1) {
+                const long long o = row + gzj;
+                p.Eout[o] = 0.f;
+                p.Eout[N + o] = 0.f;
+                p.Eout[2 * N + o] = 0.f;
+                p.Bout[o] = 0.f;
+                p.Bout[N + o] = 0.f;
+                p.Bout[2 * N + o] = 0.f;
+            }
+        }
+    }
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+__global__ void __launch_bounds__(256, 2) field_advance_rb_kernel(FieldP p) {
+    extern __shared__ float4 smem4[];
+    advance_tile_rb<NDIM, MAXM, TZ, TX, TY>(p, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<float*>(smem4));
+}
+
 template <int NDIM, int MAXM, int TZ, int TX, int TY>
 __global__ void __launch_bounds__(256) field_advance_kernel(FieldP p) {
     extern __shared__ float smem[];
@@ -258,6 +562,22 @@ cudaError_t launch_fa(const FieldP& p, cudaStream_t s) {
     using T = Tile<NDIM, MAXM, TZ, TX, TY>;
     auto k = field_advance_kernel<NDIM, MAXM, TZ, TX, TY>;
     static bool configured = false;   // attribute is per function; setting it twice is harmless
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, NDIM == 3 ? (p.g.ny + TY - 1) / TY : 1);
+    k<<<grid, 256, T::smem_bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+cudaError_t launch_fa_rb(const FieldP& p, cudaStream_t s) {
+    using T = TileRB<NDIM, MAXM, TZ, TX, TY>;
+    auto k = field_advance_rb_kernel<NDIM, MAXM, TZ, TX, TY>;
+    static bool configured = false;
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)T::smem_bytes);
@@ -366,10 +686,20 @@ cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_row
     return cudaGetLastError();
 }
 
-// Tile variants the autotuner chooses from.  2D: (TZ, TX); 3D: (TZ, TX, TY).
-//   2D: 0 = 128 x 8, 1 = 256 x 4, 2 = 64 x 16, 3 = 256 x 8
-//   3D: 0 = 64 x 4 x 4, 1 = 128 x 4 x 2, 2 = 32 x 8 x 4
-int field_variants(int ndim) { return ndim == 2 ? 4 : 3; }
+// Tile variants the autotuner chooses from.  2D: (TZ, TX); 3D: (TZ, TX, TY); rb = register-
+// blocked tile (four z cells per thread).
+//   2D: 0 = 128 x 8, 1 = 256 x 4, 2 = 64 x 16, 3 = 256 x 8,
+//       4 = rb 128 x 8, 5 = rb 256 x 4, 6 = rb 128 x 4, 7 = rb 256 x 8
+//   3D: 0 = 64 x 4 x 4, 1 = 128 x 4 x 2, 2 = 32 x 8 x 4,
+//       3 = rb 64 x 4 x 4, 4 = rb 128 x 4 x 2, 5 = rb 32 x 8 x 4
+int field_variants(int ndim) { return ndim == 2 ? 8 : 6; }
+
+// Variant used before (or without) pic_autotune: the register-blocked tile for the customised
+// stencils, the scalar tile for Yee.
+int default_field_variant(int ndim, int M) {
+    if (M <= 1) return 0;
+    return ndim == 2 ? 4 : 4;
+}
 
 namespace {
 template <int NDIM, int MAXM>
@@ -379,18 +709,30 @@ cudaError_t launch_fa_variant(const FieldP& p, int v, cudaStream_t s) {
             case 1: return launch_fa<2, MAXM, 256, 4, 1>(p, s);
             case 2: return launch_fa<2, MAXM, 64, 16, 1>(p, s);
             case 3: return launch_fa<2, MAXM, 256, 8, 1>(p, s);
+            case 4: return launch_fa_rb<2, MAXM, 128, 8, 1>(p, s);
+            case 5: return launch_fa_rb<2, MAXM, 256, 4, 1>(p, s);
+            case 6: return launch_fa_rb<2, MAXM, 128, 4, 1>(p, s);
+            case 7: return launch_fa_rb<2, MAXM, 256, 8, 1>(p, s);
             default: return launch_fa<2, MAXM, 128, 8, 1>(p, s);
         }
     }
     switch (v) {
         case 1: return launch_fa<3, MAXM, 128, 4, 2>(p, s);
         case 2: return launch_fa<3, MAXM, 32, 8, 4>(p, s);
+        case 3: return launch_fa_rb<3, MAXM, 64, 4, 4>(p, s);
+        case 4: return launch_fa_rb<3, MAXM, 128, 4, 2>(p, s);
+        case 5: return launch_fa_rb<3, MAXM, 32, 8, 4>(p, s);
         default: return launch_fa<3, MAXM, 64, 4, 4>(p, s);
     }
 }
+
+bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
 }  // namespace
 
-cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s, int variant) {
+cudaError_t launch_field_advance(const FieldP& p_in, cudaStream_t s, int variant) {
+    FieldP p = p_in;
+    p.vec4 = (p.g.nz % 4 == 0) && aligned16(p.Ein) && aligned16(p.Bin) && aligned16(p.J1) && aligned16(p.J2) &&
+             aligned16(p.J3) && aligned16(p.Eout) && aligned16(p.Bout);
     const int M = p.st.M;
     if (p.g.ndim == 2) {
         if (M <= 1) return launch_fa_variant<2, 1>(p, variant, s);

@@ -615,6 +615,11 @@ __global__ void __launch_bounds__(FUSED_T, NDIM == 3 ? 2 : 4) push_deposit_batch
 // Boxes larger than the shared-memory caps fall back to global loads / global atomics.
 constexpr int F_CAP = 6 * 1536;    // field box floats (6 components)
 constexpr int J_CAP = 3 * 1536;    // current box floats (3 components)
+constexpr int DIRECT_STEPS = 2;    // runs of up to 4 lanes deposit without the warp reduction
+
+// floor(i / d) for 0 <= i < 2^22 from r = 1/d rounded to nearest: (i + 1/2) r is within
+// (i + 1/2) 2^-23 / d of (i + 1/2) / d, which lies at least 1/(2d) from an integer.
+__device__ __forceinline__ int box_div(int i, float r) { return (int)(((float)i + 0.5f) * r); }
 
 struct SegReduce {
     bool same[5];       // lane + 2^k belongs to the same run
@@ -692,8 +697,6 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
     const long long n = *sp.count;
     const long long cap = sp.cap;
     const int N = (int)g.ncell;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = FUSED_T / 32;
     for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T) {
         if (threadIdx.x < 8) box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
         __syncthreads();
@@ -739,14 +742,13 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
         const int fvol = fzl * fxl;
         const bool ftile = any && 6 * fvol <= F_CAP && fxl <= g.nx + 2 * K;
         if (ftile) {
-            for (int r = warp; r < 6 * fxl; r += NW) {
-                const int c = r / fxl, x = r - c * fxl;
+            // one box float per thread and pass: i = (c fxl + x) fzl + z
+            const float rv = 1.f / (float)fvol, rz = 1.f / (float)fzl;
+            for (int i = threadIdx.x; i < 6 * fvol; i += FUSED_T) {
+                const int c = box_div(i, rv), rem = i - c * fvol;
+                const int x = box_div(rem, rz), gz = fz0 + rem - x * fzl;
                 const float* src = (c < 3 ? E + c * N : B + (c - 3) * N) + wrapi(fx0 + x, g.nx) * g.nz;
-                float* dst = sF + c * fvol + x * fzl;
-                for (int z = lane; z < fzl; z += 32) {
-                    const int gz = fz0 + z;
-                    dst[z] = ((unsigned)gz < (unsigned)g.nz) ? __ldg(src + gz) : 0.f;
-                }
+                sF[i] = ((unsigned)gz < (unsigned)g.nz) ? __ldg(src + gz) : 0.f;
             }
         }
         __syncthreads();
@@ -833,41 +835,61 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
             }
             // shared box: the lane's window origin in the box; global fallback: wrapped row offsets
             const int sbase = (bx - jx0) * jzl + (bz - jz0);
-            int grow[KW];
+            if (jtile && seg.steps <= DIRECT_STEPS) {
+                // short runs (at most 2^DIRECT_STEPS lanes on one node): every live lane adds its
+                // own values; the few-way address conflicts cost less than the reduction
+                float* s0 = sJ + sbase;
 #pragma unroll
-            for (int b = 0; b < KW; ++b) grow[b] = wrapi(bx + b, g.nx) * g.nz;
-            auto put = [&](int c, int a, int b, float v) {
-                v = seg.sum(v);
-                // only live lanes own a window inside the box (dead or empty slots are one-lane
-                // runs with no window; their sums are zero and they must not write)
-                if (jtile) {
-                    if (seg.head && ok && v != 0.f) atomicAdd(sJ + c * jvol + sbase + b * jzl + a, v);
-                } else {
-                    const int gz = bz + a;
-                    if (seg.head && ok && v != 0.f && (unsigned)gz < (unsigned)g.nz)
-                        atomicAdd(J + c * N + grow[b] + gz, v);
-                }
-            };
+                for (int b = 0; b < KW; ++b)
 #pragma unroll
-            for (int b = 0; b < KW; ++b)
+                    for (int a = 0; a < KW; ++a) {
+                        float v;
+                        if (a < KW - 1) {
+                            v = Cz[a] * Tx[b];
+                            if (ok && v != 0.f) atomicAdd(s0 + b * jzl + a, v);
+                        }
+                        if (b < KW - 1) {
+                            v = Tz[a] * Cx[b];
+                            if (ok && v != 0.f) atomicAdd(s0 + jvol + b * jzl + a, v);
+                        }
+                        v = S0z[a] * Ax[b] + DSz[a] * Bx[b];
+                        if (ok && v != 0.f) atomicAdd(s0 + 2 * jvol + b * jzl + a, v);
+                    }
+            } else {
+                int grow[KW];
 #pragma unroll
-                for (int a = 0; a < KW; ++a) {
-                    if (a < KW - 1) put(0, a, b, Cz[a] * Tx[b]);
-                    if (b < KW - 1) put(1, a, b, Tz[a] * Cx[b]);
-                    put(2, a, b, S0z[a] * Ax[b] + DSz[a] * Bx[b]);
-                }
+                for (int b = 0; b < KW; ++b) grow[b] = wrapi(bx + b, g.nx) * g.nz;
+                auto put = [&](int c, int a, int b, float v) {
+                    v = seg.sum(v);
+                    // only live lanes own a window inside the box (dead or empty slots are one-lane
+                    // runs with no window; their sums are zero and they must not write)
+                    if (jtile) {
+                        if (seg.head && ok && v != 0.f) atomicAdd(sJ + c * jvol + sbase + b * jzl + a, v);
+                    } else {
+                        const int gz = bz + a;
+                        if (seg.head && ok && v != 0.f && (unsigned)gz < (unsigned)g.nz)
+                            atomicAdd(J + c * N + grow[b] + gz, v);
+                    }
+                };
+#pragma unroll
+                for (int b = 0; b < KW; ++b)
+#pragma unroll
+                    for (int a = 0; a < KW; ++a) {
+                        if (a < KW - 1) put(0, a, b, Cz[a] * Tx[b]);
+                        if (b < KW - 1) put(1, a, b, Tz[a] * Cx[b]);
+                        put(2, a, b, S0z[a] * Ax[b] + DSz[a] * Bx[b]);
+                    }
+            }
         }
         __syncthreads();
         if (jtile) {
-            for (int r = warp; r < 3 * jxl; r += NW) {
-                const int c = r / jxl, x = r - c * jxl;
-                const float* src = sJ + c * jvol + x * jzl;
-                float* dst = J + c * N + wrapi(jx0 + x, g.nx) * g.nz;
-                for (int z = lane; z < jzl; z += 32) {
-                    const float val = src[z];
-                    const int gz = jz0 + z;
-                    if (val != 0.f && (unsigned)gz < (unsigned)g.nz) atomicAdd(dst + gz, val);
-                }
+            const float rv = 1.f / (float)jvol, rz = 1.f / (float)jzl;
+            for (int i = threadIdx.x; i < 3 * jvol; i += FUSED_T) {
+                const float val = sJ[i];
+                if (val == 0.f) continue;
+                const int c = box_div(i, rv), rem = i - c * jvol;
+                const int x = box_div(rem, rz), gz = jz0 + rem - x * jzl;
+                if ((unsigned)gz < (unsigned)g.nz) atomicAdd(J + c * N + wrapi(jx0 + x, g.nx) * g.nz + gz, val);
             }
         }
         __syncthreads();

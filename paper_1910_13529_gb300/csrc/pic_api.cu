@@ -66,7 +66,7 @@ struct pic_t {
     long long launches[PIC_TIMING_N] = {0};
     float* adj_scratch = nullptr; // adjoint: B', E', W (7 N floats)
     int fa_variant = 0;           // field-advance tile variant (pic_autotune)
-    double fa_ms[8] = {0};        // measured time per variant (ms), 0 = not measured
+    double fa_ms[PIC_MAX_TILE_VARIANTS] = {0};   // measured time per variant (ms), 0 = not measured
 };
 
 namespace {
@@ -346,6 +346,7 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     g.dt = (float)c.dt;
     g.shape = c.shape;
     h->st.M = M;
+    h->fa_variant = default_field_variant(c.ndim, M);
     for (int l = 0; l < PIC_MAX_M; ++l) {
         h->C64[l] = l < M ? C[l] : 0.0;
         h->st.C[l] = (float)h->C64[l];

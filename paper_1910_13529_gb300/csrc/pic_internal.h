@@ -54,6 +54,7 @@ struct FieldP {
     float* Eout;
     float* Bout;
     int shift;           // 1: write the result one cell towards -z, zero the front column
+    int vec4;            // nz % 4 == 0 and every array 16-byte aligned (set by launch_field_advance)
 };
 
 // One species' particle arrays and per-species constants.
@@ -96,6 +97,7 @@ enum : int { STATUS_CAPACITY = 1, STATUS_TIMEOUT = 2 };
 // ---- launchers (return cudaGetLastError of the launch) ----
 cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s, int variant = 0);
 int field_variants(int ndim);
+int default_field_variant(int ndim, int M);
 cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s);
 // batched: instance tables live in device memory
 cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,

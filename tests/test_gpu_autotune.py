@@ -39,3 +39,55 @@ def test_autotune_keeps_state_and_result(nd, solver, C):
         sim.field_advance()
         assert field_error(sim, osim) < 1e-5, v
     sim.close()
+
+
+VARIANT_CASES = [
+    # (ndim, nz, nx, ny, solver, coefficients): nz % 4 != 0 takes the scalar edge path of the
+    # register-blocked tiles; nx, ny smaller than a tile make the x/y halos wrap around.
+    (2, 203, 11, 1, "custom", TABLE1),
+    (2, 130, 4, 1, "yee", None),
+    (3, 101, 6, 5, "custom", "fit8"),
+    (3, 64, 9, 4, "custom", TABLE1),
+]
+
+
+@pytest.mark.parametrize("nd,nz,nx,ny,solver,C", VARIANT_CASES)
+@pytest.mark.parametrize("moving", [False, True])
+def test_every_tile_variant_matches_oracle(nd, nz, nx, ny, solver, C, moving):
+    from oracle import fit
+    from paper_1910_13529_gb300 import pic_get_tuning, pic_set_tuning
+
+    if isinstance(C, str):
+        C = fit.fit_coefficients(2.0, M=8)
+    d = (0.5, 0.4, 0.45)
+    dt = 0.9 * fit.cfl_dt(d[0], [d[1]] + ([d[2]] if nd == 3 else []), C)
+    if moving:
+        dt = min(dt, 0.6 * d[0])
+    grid = dict(ndim=nd, nz=nz, nx=nx, ny=ny, dz=d[0], dx=d[1], dy=d[2], dt=dt, solver=solver, shape=1,
+                moving_window=moving)
+    osim = oracle_sim(grid, [], coef=C)
+    rng = np.random.default_rng(nz + 7 * nx)
+    init = [rng.normal(size=a.shape).astype(np.float32) for a in (osim.E, osim.B, osim.J)]
+    osim.E[:], osim.B[:], osim.J[:] = init
+    nsteps = 4
+    for _ in range(nsteps):
+        oc.field_advance(osim.g, osim.E, osim.B, osim.J)
+        osim.n += 1
+        if moving and oc.window_due(osim.n, osim.g.dt, osim.g.dz, osim.shifts):
+            osim.shift()
+    if moving:
+        assert osim.shifts >= 1
+    sim = gpu_sim(grid, [], coef=C)
+    nv = len(pic_get_tuning(sim.h)[1])
+    assert nv == (8 if nd == 2 else 6)
+    sim.close()
+    for v in range(nv):
+        sim = gpu_sim(grid, [], coef=C)
+        pic_set_tuning(sim.h, v)
+        for a, x in zip((sim.E, sim.B, sim.J), init):
+            a.copy_(torch.from_numpy(x))
+        for _ in range(nsteps):
+            sim.field_advance()
+        assert sim.state()[1] == osim.shifts
+        assert field_error(sim, osim) < 1e-5, v
+        sim.close()
