@@ -31,6 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 BYTES_PER_PUSH_2D = 48          # read + write cell (4) + offsets (2 x 4) + u (3 x 4)
+BYTES_PER_PUSH_3D = 56          # read + write cell (4) + offsets (3 x 4) + u (3 x 4)
 BYTES_PER_CELL_UPDATE = 60      # read E, B, J (9 x 4) + write E, B (6 x 4)
 METRIC = "cell-updates/s and particle-pushes/s (% HBM roofline) at <=1e-5 rel err vs FP64"
 
@@ -43,17 +44,23 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="reduced grid (profiling captures)")
-    ap.add_argument("--workload", default="beam2d", choices=["beam2d", "batch", "fields"],
-                    help="beam2d: the bench workload; batch: 256 independent single-particle runs, "
-                         "batched launch vs per-instance launches")
+    ap.add_argument("--workload", default="beam2d", choices=["beam2d", "beam3d", "batch", "fields"],
+                    help="beam2d: the bench workload; beam3d: the 3D 512 x 256 x 256 beam in plasma; "
+                         "batch: 256 independent single-particle runs, batched launch vs per-instance "
+                         "launches; fields: the field advance alone on grids above L2")
     return ap.parse_args()
 
 
-def workload(small=False):
+def workload(args):
+    """(grid, species, name) of the timed run."""
     from paper_1910_13529_gb300 import workloads as wl
-    if small:
-        return wl.beam_plasma(ndim=2, nz=512, nx=256, n_beam=250_000, behind_front=3.0)
-    return wl.beam_plasma()
+    if args.workload == "beam3d":
+        if args.small:
+            return wl.beam_plasma_3d(nz=256, nx=128, ny=128, n_beam=500_000), "beam_plasma_3d_small"
+        return wl.beam_plasma_3d(), "beam_plasma_3d"
+    if args.small:
+        return wl.beam_plasma(ndim=2, nz=512, nx=256, n_beam=250_000, behind_front=3.0), "beam_plasma_2d_small"
+    return wl.beam_plasma(), "beam_plasma_2d"
 
 
 def measured_peak():
@@ -150,6 +157,35 @@ def emit(obj):
     print(json.dumps(obj), flush=True)
 
 
+# ncu summaries committed under profiles/ that carry the DRAM traffic of a kernel class, with the
+# SHA-1 of the source file the capture was built from
+TRAFFIC_SOURCES = {
+    ("particles", 2): ("profiles/push_deposit_2d_beam_plasma_2d.md", "paper_1910_13529_gb300/csrc/particle_kernels.cu"),
+    ("particles", 3): ("profiles/push_deposit_3d_beam_plasma_3d.md", "paper_1910_13529_gb300/csrc/particle_kernels.cu"),
+}
+
+
+def captured_traffic(kind, ndim):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu summary, or
+    None when there is none or the kernel source has changed since the capture."""
+    import hashlib
+    import re
+    entry = TRAFFIC_SOURCES.get((kind, ndim))
+    if entry is None:
+        return None
+    md, src = (os.path.join(ROOT, q) for q in entry)
+    try:
+        text = open(md).read()
+        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
+    if not m or not h or h.group(1) != digest:
+        return None
+    return float(m.group(1))
+
+
 def aggregate(ms, pushes_per_step, steps, world, device=None):
     """Whole-job throughput of independent replicas: the slowest rank's time and the work of all
     ranks (each rank runs its own replica, no collective on the data path).  Returns
@@ -171,11 +207,10 @@ def aggregate(ms, pushes_per_step, steps, world, device=None):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    grid, sps = workload(args.small)
+    (grid, sps), wname = workload(args)
     n_total = sum(len(sp["iz"]) for sp in sps)
     vals, times = [], []
-    for _ in range(max(args.warmup, 0) and 0 or 0):
-        pass
+    # the oracle has nothing to warm up; at most three timed samples keep the run within minutes
     for k in range(max(1, min(args.steps, 3))):
         v, dt, n = oracle_baseline(grid, sps, frac=0.05, seed=k)
         vals.append(v)
@@ -187,7 +222,8 @@ def run_reference(args, rank, world):
           "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 * float(np.median(times)),
           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
           "data": "synthetic",
-          "config": {"workload": "beam_plasma_2d", "grid": [grid["nz"], grid["nx"]], "particles": n_total},
+          "config": {"workload": wname, "grid": [grid["nz"], grid["nx"]] + ([grid["ny"]] if grid["ndim"] == 3 else []),
+                     "particles": n_total},
           "cpu_baseline": {"value": value, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
                            "sample": sample},
           "e2e": {"value": value, "unit": "particle-pushes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
@@ -201,9 +237,11 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device(f"cuda:{local_rank}")
     torch.cuda.set_device(dev)
-    grid, sps = workload(args.small)
+    (grid, sps), wname = workload(args)
+    nd = grid["ndim"]
+    bpp = BYTES_PER_PUSH_3D if nd == 3 else BYTES_PER_PUSH_2D
     n0 = [len(sp["iz"]) for sp in sps]
-    cap_extra = 200_000
+    cap_extra = 200_000 if nd == 2 else 4_000_000    # injection between two compacting sorts
     kw = {k: grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape", "solver",
                                "moving_window", "inject_species", "inject_ppc", "rho_bg")}
     sim = Simulation(device=str(dev), sort_every=20, **kw)
@@ -242,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kms, key=kms.get)
     peak, peak_kind = measured_peak()
     if dom == "particles":
-        algo = BYTES_PER_PUSH_2D * pushes_per_step * args.steps
+        algo = bpp * pushes_per_step * args.steps
     else:
         algo = BYTES_PER_CELL_UPDATE * cells * args.steps
     achieved = algo / (kms[dom] / 1e3) / 1e9
@@ -294,20 +332,21 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = total_pushes / (float(t.item()) / 1e3)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 2:
         v, dt, n = oracle_baseline(grid, sps, frac=0.05)
         cpu = {"value": v, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
                "sample": f"one FP64 oracle step, full {grid['nz']}x{grid['nx']} grid, 5% random particle "
                          f"sample ({n} particles), {dt:.1f} s single-threaded"}
     if rank == 0:
         launches = int(sum(klaunch.values()))
-        working = (sum(sim.species[s]["cap"] for s in sim.species) * 24 + cells * 4 * (6 + 6 + 3)) / 1e6
+        working = (sum(sim.species[s]["cap"] for s in sim.species) * (bpp // 2) + cells * 4 * (6 + 6 + 3)) / 1e6
         emit({"metric": METRIC, "value": value, "unit": "particle-pushes/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic (seeded beam + quiet-start plasma)",
-              "config": {"workload": "beam_plasma_2d" if not args.small else "beam_plasma_2d_small",
-                         "grid": [grid["nz"], grid["nx"]], "particles": int(sum(n0)), "solver": "custom M=16",
+              "config": {"workload": wname,
+                         "grid": [grid["nz"], grid["nx"]] + ([grid["ny"]] if nd == 3 else []),
+                         "particles": int(sum(n0)), "solver": "custom M=16",
                          "shape": "quadratic", "moving_window": True, "sort_every": 20,
                          "l2": f"inputs larger than L2 (working set {working:.0f} MB > 129 MB)",
                          "parallelism": f"{world} independent replica(s)",
@@ -316,9 +355,8 @@ def run_ours(args, rank, world, local_rank):
                             "field_advance_GBps": fa_gbs,
                             "kernel_ms": kms, "kernel_launches": klaunch},
               "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                           "algorithmic_bytes_per_unit": BYTES_PER_PUSH_2D if dom == "particles"
-                           else BYTES_PER_CELL_UPDATE},
+                           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": captured_traffic(dom, nd),
+                           "algorithmic_bytes_per_unit": bpp if dom == "particles" else BYTES_PER_CELL_UPDATE},
               "cpu_baseline": cpu,
               "e2e": {"value": e2e_value, "unit": "particle-pushes/s", "h2d_bytes_per_step": h2d / args.steps,
                       "d2h_bytes_per_step": d2h / args.steps},

@@ -242,9 +242,10 @@ pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const floa
  * PIC_MAX_TILE_VARIANTS entries) and the number of variants.  2D (z x x): 0 = 128x8,
  * 1 = 256x4, 2 = 64x16, 3 = 256x8 with one cell per thread and stage, 4 = 128x8, 5 = 256x4,
  * 6 = 128x4, 7 = 256x8 register-blocked (four z cells per thread, 128-bit shared loads);
- * 3D (z x x x y): 0 = 64x4x4, 1 = 128x4x2, 2 = 32x8x4, and 3..5 the same shapes
- * register-blocked.  Without pic_autotune a handle uses 0 for Yee and the register-blocked
- * 128x8 (2D) or 128x4x2 (3D) tile for customised stencils.  */
+ * 3D (z x x x y): 0 = 64x4x4, 1 = 128x4x2, 2 = 32x8x4, 3..5 the same shapes register-
+ * blocked, 6..9 register-blocked columns that march along y (z x x = 128x4 with 256 or 128
+ * threads, 128x8, 64x8).  Without pic_autotune a handle uses 0 for Yee and the register-
+ * blocked 128x8 (2D) or y-marching 128x4 (3D) tile for customised stencils.  */
 #define PIC_MAX_TILE_VARIANTS 16
 pic_status pic_autotune(pic_t* h, void* stream);
 pic_status pic_get_tuning(const pic_t* h, int* variant, double* ms, int* nvariants);

@@ -523,6 +523,278 @@ __global__ void __launch_bounds__(256, 2) field_advance_rb_kernel(FieldP p) {
     advance_tile_rb<NDIM, MAXM, TZ, TX, TY>(p, blockIdx.x, blockIdx.y, blockIdx.z, reinterpret_cast<float*>(smem4));
 }
 
+
+// ---- 3D y-marching tile -----------------------------------------------------------------
+// A CTA owns a TZ x TX column of x-z planes and walks y over [ya, ya + yc), keeping three E
+// planes, two B planes and one J plane in shared memory, register-blocked along z as above.
+// For output plane k it stages E^n(k+2), B^n(k+1), J(k+1), then computes
+//   B^{n+1/2}(k+1) from E^n(k+1), E^n(k+2);
+//   E^{n+1}(k+1)   from B^{n+1/2}(k+1), B^{n+1/2}(k) (in place over E^n(k+1));
+//   B^{n+1}(k)     from E^{n+1}(k), E^{n+1}(k+1), B^{n+1/2}(k), and stores E^{n+1}(k), B^{n+1}(k).
+// Every plane is read once per CTA plus its x halo, where a tile blocked in x and y re-reads
+// and recomputes a (T+3)^2 / T^2 halo.
+template <int MAXM, int TZ, int TX>
+struct MarchT {
+    static constexpr int MP = (MAXM + 3) & ~3;
+    static constexpr int H2 = MP, H1 = 2 * MP, H0 = 3 * MP;
+    static constexpr int WE = TZ + 2 * H0, WB = TZ + 2 * H1, WJ = TZ + 2 * H2;
+    static constexpr int RX0 = TX + 3, RX1 = TX + 2, RX2 = TX + 1;    // E rows [-1, TX+1], B [-1, TX], J [0, TX]
+    static constexpr int PE = RX0 * WE, PB = RX1 * WB, PJ = RX2 * WJ;  // one component of one plane
+    static constexpr size_t smem_bytes = sizeof(float) * 3 * (3 * PE + 2 * PB + PJ);
+    static_assert(TZ % 4 == 0, "the z tile holds whole groups of four cells");
+};
+
+// One x-z plane (global y = gy) of components f0..f2: `rows` rows starting at x0 + dx, z in
+// [zlo, zlo + w), into dst[c * cstride + r * w + col]; zero outside 0 <= z < nz.
+__device__ __forceinline__ void stage_plane(float* dst, int cstride, const float* __restrict__ f0,
+                                            const float* __restrict__ f1, const float* __restrict__ f2, int rows,
+                                            int w, int zlo, int x0, int dx, int gy, const GridP& g, bool vec) {
+    const float* f[3] = {f0, f1, f2};
+    const int ng = w >> 2;
+    for (int it = threadIdx.x; it < rows * ng; it += blockDim.x) {
+        const int gi = it % ng, r = it / ng;
+        const int gz = zlo + 4 * gi;
+        const long long row = ((long long)gy * g.nx + wrapi(x0 + r + dx, g.nx)) * g.nz;
+        float* d = dst + r * w + 4 * gi;
+        if (vec) {
+            const bool in = gz >= 0 && gz < g.nz;
+            const long long o = in ? row + gz : 0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) cp_async16(d + c * cstride, f[c] + o, in);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float a[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    a[j] = (gz + j >= 0 && gz + j < g.nz) ? __ldg(f[c] + row + gz + j) : 0.f;
+                sts4(d + c * cstride, a);
+            }
+        }
+    }
+}
+
+// B^{n+1/2} in place over B^n plane b (rows x in [-1, TX]) from E^n planes e (y) and e1 (y+1).
+template <int MAXM, int TZ, int TX>
+__device__ __forceinline__ void march_bhalf(const FieldP& p, float* b, const float* e, const float* e1, int z0) {
+    using T = MarchT<MAXM, TZ, TX>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, PE = T::PE, PB = T::PB, NG = WB / 4;
+    const GridP& g = p.g;
+    const float hz = 0.5f * g.dt / g.dz, hx = 0.5f * g.dt / g.dx, hy = 0.5f * g.dt / g.dy;
+    for (int it = threadIdx.x; it < T::RX1 * NG; it += blockDim.x) {
+        const int gi = it % NG, rx = it / NG;
+        const int z = 4 * gi - T::H1, gz = z0 + z;
+        if (gz + 3 < 0 || gz >= g.nz) continue;                     // B^n = B^{n+1/2} = 0 there
+        const int eo = rx * WE + z + T::H0;
+        float d2[4], d3[4], E2[4], E3[4], E1[4], E1x[4], E3x[4], E1y[4], E2y[4];
+        window_dz<MAXM, MP, true>(p.st, e + PE + eo - MP, d2, E2);
+        window_dz<MAXM, MP, true>(p.st, e + 2 * PE + eo - MP, d3, E3);
+        lds4(E1, e + eo);
+        lds4(E1x, e + eo + WE);
+        lds4(E3x, e + 2 * PE + eo + WE);
+        lds4(E1y, e1 + eo);
+        lds4(E2y, e1 + PE + eo);
+        const int bo = rx * WB + 4 * gi;
+        float b0[4], b1[4], b2[4];
+        lds4(b0, b + bo);
+        lds4(b1, b + PB + bo);
+        lds4(b2, b + 2 * PB + bo);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = gz + j >= 0 && gz + j < g.nz;
+            b0[j] = in ? b0[j] - (hx * (E3x[j] - E3[j]) - hy * (E2y[j] - E2[j])) : 0.f;
+            b1[j] = in ? b1[j] - (hy * (E1y[j] - E1[j]) - hz * d3[j]) : 0.f;
+            b2[j] = in ? b2[j] - (hz * d2[j] - hx * (E1x[j] - E1[j])) : 0.f;
+        }
+        sts4(b + bo, b0);
+        sts4(b + PB + bo, b1);
+        sts4(b + 2 * PB + bo, b2);
+    }
+}
+
+// E^{n+1} in place over E^n plane e (rows x in [0, TX]) from B^{n+1/2} planes b (y), bm (y-1)
+// and the J plane j.
+template <int MAXM, int TZ, int TX>
+__device__ __forceinline__ void march_enew(const FieldP& p, float* e, const float* b, const float* bm,
+                                           const float* j, int z0) {
+    using T = MarchT<MAXM, TZ, TX>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, WJ = T::WJ, PE = T::PE, PB = T::PB, PJ = T::PJ;
+    constexpr int NG = WJ / 4;
+    const GridP& g = p.g;
+    const float dt = g.dt, fz = dt / g.dz, fx = dt / g.dx, fy = dt / g.dy;
+    for (int it = threadIdx.x; it < T::RX2 * NG; it += blockDim.x) {
+        const int gi = it % NG, rx = it / NG;
+        const int z = 4 * gi - T::H2, gz = z0 + z;
+        if (gz + 3 < 0 || gz >= g.nz) continue;                     // E^n = E^{n+1} = 0 there
+        const int eo = (rx + 1) * WE + z + T::H0;
+        const int bo = (rx + 1) * WB + z + T::H1;
+        float d2[4], d3[4], B2[4], B3[4], B1[4], B1x[4], B3x[4], B1y[4], B2y[4];
+        window_dz<MAXM, MP, false>(p.st, b + PB + bo - MP, d2, B2);
+        window_dz<MAXM, MP, false>(p.st, b + 2 * PB + bo - MP, d3, B3);
+        lds4(B1, b + bo);
+        lds4(B1x, b + bo - WB);
+        lds4(B3x, b + 2 * PB + bo - WB);
+        lds4(B1y, bm + bo);
+        lds4(B2y, bm + PB + bo);
+        const int jo = rx * WJ + 4 * gi;
+        float e0[4], e1[4], e2[4], j0[4], j1[4], j2[4];
+        lds4(e0, e + eo);
+        lds4(e1, e + PE + eo);
+        lds4(e2, e + 2 * PE + eo);
+        lds4(j0, j + jo);
+        lds4(j1, j + PJ + jo);
+        lds4(j2, j + 2 * PJ + jo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool in = gz + q >= 0 && gz + q < g.nz;
+            e0[q] = in ? e0[q] + (fx * (B3[q] - B3x[q]) - fy * (B2[q] - B2y[q])) - dt * j0[q] : 0.f;
+            e1[q] = in ? e1[q] + (fy * (B1[q] - B1y[q]) - fz * d3[q]) - dt * j1[q] : 0.f;
+            e2[q] = in ? e2[q] + (fz * d2[q] - fx * (B1[q] - B1x[q])) - dt * j2[q] : 0.f;
+        }
+        sts4(e + eo, e0);
+        sts4(e + PE + eo, e1);
+        sts4(e + 2 * PE + eo, e2);
+    }
+}
+
+// B^{n+1} on the tile rows (x in [0, TX)) of plane gy from E^{n+1} planes e (y), e1 (y+1) and
+// B^{n+1/2} plane b; stores E^{n+1}(y) and B^{n+1}(y) (one cell towards -z if the window moves).
+template <int MAXM, int TZ, int TX>
+__device__ __forceinline__ void march_bnew_store(const FieldP& p, const float* e, const float* e1, const float* b,
+                                                 int z0, int x0, int gy, bool vec) {
+    using T = MarchT<MAXM, TZ, TX>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, PE = T::PE, PB = T::PB, NG = TZ / 4;
+    const GridP& g = p.g;
+    const long long N = g.ncell;
+    const float hz = 0.5f * g.dt / g.dz, hx = 0.5f * g.dt / g.dx, hy = 0.5f * g.dt / g.dy;
+    for (int it = threadIdx.x; it < TX * NG; it += blockDim.x) {
+        const int gi = it % NG, x = it / NG;
+        const int z = 4 * gi, gz = z0 + z, gx = x0 + x;
+        if (gz >= g.nz || gx >= g.nx) continue;
+        const int eo = (x + 1) * WE + z + T::H0;
+        const int bo = (x + 1) * WB + z + T::H1;
+        float d2[4], d3[4], E2[4], E3[4], E1[4], E1x[4], E3x[4], E1y[4], E2y[4];
+        window_dz<MAXM, MP, true>(p.st, e + PE + eo - MP, d2, E2);
+        window_dz<MAXM, MP, true>(p.st, e + 2 * PE + eo - MP, d3, E3);
+        lds4(E1, e + eo);
+        lds4(E1x, e + eo + WE);
+        lds4(E3x, e + 2 * PE + eo + WE);
+        lds4(E1y, e1 + eo);
+        lds4(E2y, e1 + PE + eo);
+        float b0[4], b1[4], b2[4];
+        lds4(b0, b + bo);
+        lds4(b1, b + PB + bo);
+        lds4(b2, b + 2 * PB + bo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            b0[q] -= hx * (E3x[q] - E3[q]) - hy * (E2y[q] - E2[q]);
+            b1[q] -= hy * (E1y[q] - E1[q]) - hz * d3[q];
+            b2[q] -= hz * d2[q] - hx * (E1x[q] - E1[q]);
+        }
+        const long long row = ((long long)gy * g.nx + gx) * g.nz;
+        if (vec && !p.shift) {
+            const long long o = row + gz;
+            *reinterpret_cast<float4*>(p.Eout + o) = make_float4(E1[0], E1[1], E1[2], E1[3]);
+            *reinterpret_cast<float4*>(p.Eout + N + o) = make_float4(E2[0], E2[1], E2[2], E2[3]);
+            *reinterpret_cast<float4*>(p.Eout + 2 * N + o) = make_float4(E3[0], E3[1], E3[2], E3[3]);
+            *reinterpret_cast<float4*>(p.Bout + o) = make_float4(b0[0], b0[1], b0[2], b0[3]);
+            *reinterpret_cast<float4*>(p.Bout + N + o) = make_float4(b1[0], b1[1], b1[2], b1[3]);
+            *reinterpret_cast<float4*>(p.Bout + 2 * N + o) = make_float4(b2[0], b2[1], b2[2], b2[3]);
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gzq = gz + q;
+            if (gzq >= g.nz) break;
+            const int oz = gzq - p.shift;
+            if (oz >= 0) {
+                const long long o = row + oz;
+                p.Eout[o] = E1[q];
+                p.Eout[N + o] = E2[q];
+                p.Eout[2 * N + o] = E3[q];
+                p.Bout[o] = b0[q];
+                p.Bout[N + o] = b1[q];
+                p.Bout[2 * N + o] = b2[q];
+            }
+            if (p.shift && gzq == g.nz - 1) {
+                const long long o = row + gzq;
+                p.Eout[o] = 0.f;
+                p.Eout[N + o] = 0.f;
+                p.Eout[2 * N + o] = 0.f;
+                p.Bout[o] = 0.f;
+                p.Bout[N + o] = 0.f;
+                p.Bout[2 * N + o] = 0.f;
+            }
+        }
+    }
+}
+
+template <int MAXM, int TZ, int TX, int NT>
+__global__ void __launch_bounds__(NT) field_advance_march_kernel(FieldP p, int yc) {
+    using T = MarchT<MAXM, TZ, TX>;
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    float* const sB0 = sm + 9 * T::PE;
+    float* const sJ = sB0 + 6 * T::PB;
+    const GridP& g = p.g;
+    const long long N = g.ncell;
+    const bool vec = p.vec4 != 0;
+    const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TX;
+    const int ya = blockIdx.z * yc, yb = min(ya + yc, g.ny);
+    auto Eslot = [&](int i) { return sm + i * 3 * T::PE; };
+    auto Bslot = [&](int i) { return sB0 + i * 3 * T::PB; };
+    auto stageE = [&](int i, int y) {
+        stage_plane(Eslot(i), T::PE, p.Ein, p.Ein + N, p.Ein + 2 * N, T::RX0, T::WE, z0 - T::H0, x0, -1,
+                    wrapi(y, g.ny), g, vec);
+    };
+    auto stageB = [&](int i, int y) {
+        stage_plane(Bslot(i), T::PB, p.Bin, p.Bin + N, p.Bin + 2 * N, T::RX1, T::WB, z0 - T::H1, x0, -1,
+                    wrapi(y, g.ny), g, vec);
+    };
+    auto stageJ = [&](int y) {
+        stage_plane(sJ, T::PJ, p.J1, p.J2, p.J3, T::RX2, T::WJ, z0 - T::H2, x0, 0, wrapi(y, g.ny), g, vec);
+    };
+    auto landed = [&]() {
+        if (vec) cp_async_wait_all();
+        __syncthreads();
+    };
+    // prologue: B^{n+1/2}(ya-1), B^{n+1/2}(ya), E^{n+1}(ya)
+    stageE(0, ya - 1);
+    stageE(1, ya);
+    stageB(0, ya - 1);
+    landed();
+    march_bhalf<MAXM, TZ, TX>(p, Bslot(0), Eslot(0), Eslot(1), z0);
+    stageE(2, ya + 1);
+    stageB(1, ya);
+    stageJ(ya);
+    landed();
+    march_bhalf<MAXM, TZ, TX>(p, Bslot(1), Eslot(1), Eslot(2), z0);
+    __syncthreads();
+    march_enew<MAXM, TZ, TX>(p, Eslot(1), Bslot(1), Bslot(0), sJ, z0);
+    __syncthreads();
+    // E slots: ec = E^{n+1}(k), en = E^n(k+1), ef = free; B slots: bc = B^{n+1/2}(k), bf = free
+    int ec = 1, en = 2, ef = 0, bc = 1, bf = 0;
+    for (int k = ya; k < yb; ++k) {
+        stageE(ef, k + 2);
+        stageB(bf, k + 1);
+        stageJ(k + 1);
+        landed();
+        march_bhalf<MAXM, TZ, TX>(p, Bslot(bf), Eslot(en), Eslot(ef), z0);
+        __syncthreads();
+        march_enew<MAXM, TZ, TX>(p, Eslot(en), Bslot(bf), Bslot(bc), sJ, z0);
+        __syncthreads();
+        march_bnew_store<MAXM, TZ, TX>(p, Eslot(ec), Eslot(en), Bslot(bc), z0, x0, k, vec);
+        __syncthreads();
+        const int t = ec;
+        ec = en;
+        en = ef;
+        ef = t;
+        const int u = bc;
+        bc = bf;
+        bf = u;
+    }
+}
+
 template <int NDIM, int MAXM, int TZ, int TX, int TY>
 __global__ void __launch_bounds__(256) field_advance_kernel(FieldP p) {
     extern __shared__ float smem[];
@@ -586,6 +858,32 @@ cudaError_t launch_fa_rb(const FieldP& p, cudaStream_t s) {
     }
     dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, NDIM == 3 ? (p.g.ny + TY - 1) / TY : 1);
     k<<<grid, 256, T::smem_bytes, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int MAXM, int TZ, int TX, int NT>
+cudaError_t launch_fa_march(const FieldP& p, cudaStream_t s) {
+    using T = MarchT<MAXM, TZ, TX>;
+    auto k = field_advance_march_kernel<MAXM, TZ, TX, NT>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // y chunks: about four waves of CTAs over the SMs, each chunk at least 8 planes
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int cols = ((p.g.nz + TZ - 1) / TZ) * ((p.g.nx + TX - 1) / TX);
+    const int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
+    const long long want = 4LL * nsm * (per_sm > 0 ? per_sm : 1);
+    int chunks = (int)((want + cols - 1) / cols);
+    chunks = chunks < 1 ? 1 : chunks;
+    int yc = (p.g.ny + chunks - 1) / chunks;
+    yc = yc < 8 ? 8 : yc;
+    dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, (p.g.ny + yc - 1) / yc);
+    k<<<grid, NT, T::smem_bytes, s>>>(p, yc);
     return cudaGetLastError();
 }
 
@@ -691,14 +989,16 @@ cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_row
 //   2D: 0 = 128 x 8, 1 = 256 x 4, 2 = 64 x 16, 3 = 256 x 8,
 //       4 = rb 128 x 8, 5 = rb 256 x 4, 6 = rb 128 x 4, 7 = rb 256 x 8
 //   3D: 0 = 64 x 4 x 4, 1 = 128 x 4 x 2, 2 = 32 x 8 x 4,
-//       3 = rb 64 x 4 x 4, 4 = rb 128 x 4 x 2, 5 = rb 32 x 8 x 4
-int field_variants(int ndim) { return ndim == 2 ? 8 : 6; }
+//       3 = rb 64 x 4 x 4, 4 = rb 128 x 4 x 2, 5 = rb 32 x 8 x 4,
+//       6 = y-march 128 x 4 (256 threads), 7 = y-march 128 x 4 (128 threads),
+//       8 = y-march 128 x 8 (256 threads), 9 = y-march 64 x 8 (256 threads)
+int field_variants(int ndim) { return ndim == 2 ? 8 : 10; }
 
 // Variant used before (or without) pic_autotune: the register-blocked tile for the customised
 // stencils, the scalar tile for Yee.
 int default_field_variant(int ndim, int M) {
     if (M <= 1) return 0;
-    return ndim == 2 ? 4 : 4;
+    return ndim == 2 ? 4 : 6;
 }
 
 namespace {
@@ -722,6 +1022,10 @@ cudaError_t launch_fa_variant(const FieldP& p, int v, cudaStream_t s) {
         case 3: return launch_fa_rb<3, MAXM, 64, 4, 4>(p, s);
         case 4: return launch_fa_rb<3, MAXM, 128, 4, 2>(p, s);
         case 5: return launch_fa_rb<3, MAXM, 32, 8, 4>(p, s);
+        case 6: return launch_fa_march<MAXM, 128, 4, 256>(p, s);
+        case 7: return launch_fa_march<MAXM, 128, 4, 128>(p, s);
+        case 8: return launch_fa_march<MAXM, 128, 8, 256>(p, s);
+        case 9: return launch_fa_march<MAXM, 64, 8, 256>(p, s);
         default: return launch_fa<3, MAXM, 64, 4, 4>(p, s);
     }
 }

@@ -174,13 +174,15 @@ __device__ __forceinline__ void gather(const GridP& g, const float* __restrict__
 }
 
 // ---------------------------------------------------------------- push ----
+// The rotation factors use the approximate reciprocal square root and divide (a few ulp); the
+// momentum they produce is still within FP32 round-off of the exact rotation, while positions
+// take their accuracy from the float-float displacement below.
 __device__ __forceinline__ void boris(float eps, const float* eb, float* u) {
     float um0 = u[0] + eps * eb[0], um1 = u[1] + eps * eb[1], um2 = u[2] + eps * eb[2];
-    float gm = sqrtf(1.f + um0 * um0 + um1 * um1 + um2 * um2);
-    float f = eps / gm;
+    float f = eps * rsqrtf(1.f + um0 * um0 + um1 * um1 + um2 * um2);     // eps / gamma^-
     float t0 = f * eb[3], t1 = f * eb[4], t2 = f * eb[5];
     float tt = t0 * t0 + t1 * t1 + t2 * t2;
-    float sf = 2.f / (1.f + tt);
+    float sf = __fdividef(2.f, 1.f + tt);
     float s0 = sf * t0, s1 = sf * t1, s2 = sf * t2;
     float up0 = um0 + (um1 * t2 - um2 * t1);
     float up1 = um1 + (um2 * t0 - um0 * t2);
@@ -204,8 +206,9 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
     e = fmaf(a, b, -p);
 }
 
-// gamma = sqrt(1 + |u|^2) as an unevaluated float-float sum gh + gl.
-__device__ __forceinline__ void gamma_ff(const float* u, float& gh, float& gl) {
+// gamma = sqrt(1 + |u|^2) as an unevaluated float-float sum gh + gl; rg ~ 1/gh (approximate:
+// every use below corrects or tolerates its few-ulp error).
+__device__ __forceinline__ void gamma_ff(const float* u, float& gh, float& gl, float& rg) {
     float sh = 1.f, sl = 0.f;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -219,17 +222,17 @@ __device__ __forceinline__ void gamma_ff(const float* u, float& gh, float& gl) {
     sl = sl - (t - sh);
     sh = t;
     gh = sqrtf(sh);
-    gl = (fmaf(-gh, gh, sh) + sl) * (0.5f / gh);
+    rg = __fdividef(1.f, gh);
+    gl = (fmaf(-gh, gh, sh) + sl) * (0.5f * rg);
 }
 
 // Displacement u_a dt / (gamma h_a) in cells as dh + dl (k = dt/h_a given as kh + kl).  Computed
 // to ~1e-13 relative so that the per-step FP32 rounding of the offset is the only error left:
 // rounding to nearest of o + (dh + dl) is unbiased, while a once-rounded FP32 increment would
 // drift by the same fraction of an ulp every step.
-__device__ __forceinline__ void displacement(float ua, float gh, float gl, float kh, float kl, float& dh,
+__device__ __forceinline__ void displacement(float ua, float gh, float gl, float rg, float kh, float kl, float& dh,
                                              float& dl) {
-    // one reciprocal; the exact FMA residual ua - qh gh corrects whatever rounding qh carries
-    const float rg = __frcp_rn(gh);
+    // the exact FMA residual ua - qh gh corrects whatever rounding qh = ua rg carries
     float qh = ua * rg;
     float ql = (fmaf(-qh, gh, ua) - qh * gl) * rg;
     dh = qh * kh;
@@ -261,7 +264,6 @@ __device__ __forceinline__ void advance_axis(int& i, float& o, float dh, float d
 // ---------------------------------------------------------------- deposit ----
 // Current accumulators: add(component, node z, node x, node y, value) with x, y not yet wrapped.
 struct GlobalAcc {
-    static constexpr bool kAll = false;     // zero contributions are skipped
     const GridP* g;
     float* J;
     __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
@@ -270,36 +272,25 @@ struct GlobalAcc {
         atomicAdd(J + c * (int)g->ncell + o, v);
     }
 };
-// A box of nodes [z0, z0+zl) x [x0, x0+xl) x [y0, y0+yl) in shared memory, 3 components.
-struct SharedAcc {
-    static constexpr bool kAll = false;
-    float* s;
-    int z0, x0, y0, zl, xl, vol;
-    __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
-        atomicAdd(s + c * vol + ((gy - y0) * xl + (gx - x0)) * zl + (gz - z0), v);
-    }
-};
-
-// All 32 lanes of a warp deposit into the same window: sum each contribution over the warp
-// and let lane 0 add it once (dense beams put many particles of a warp in one cell, and
-// their shared-memory atomics would otherwise serialise on the same addresses).
-struct WarpSharedAcc {
-    static constexpr bool kAll = true;      // every lane calls add() in lockstep
-    SharedAcc inner;
-    bool leader;
-    __device__ __forceinline__ void add(int c, int gz, int gx, int gy, float v) const {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (leader && v != 0.f) inner.add(c, gz, gx, gy, v);
-    }
-};
-
-// first node of the deposition window of a move (the lower of the two shape supports)
+// Old-position weights w0 (first node b0) and the new position (i1, o1) -> the deposition
+// window: S0 = old weights and DS = new - old, both placed in the K + 1 nodes from the lower
+// of the two supports (returned).
 template <int SHAPE>
-__device__ __forceinline__ int window_base(int i0, float o0, int i1, float o1) {
-    float w[Shape<SHAPE>::K];
-    int b0 = i0 + Shape<SHAPE>::w(o0, w);
-    int b1 = i1 + Shape<SHAPE>::w(o1, w);
+__device__ __forceinline__ int axis_weights_from(int b0, const float* w0, int i1, float o1, float* S0, float* DS) {
+    constexpr int K = Shape<SHAPE>::K;
+    constexpr int KW = K + 1;
+    float w1[K];
+    const int b1 = i1 + Shape<SHAPE>::w(o1, w1);
+    const bool sh0 = b0 > b1, sh1 = b1 > b0;
+#pragma unroll
+    for (int k = 0; k < KW; ++k) {
+        const float a0 = k < K ? w0[k] : 0.f, a1 = k >= 1 ? w0[k - 1] : 0.f;
+        const float c0 = k < K ? w1[k] : 0.f, c1 = k >= 1 ? w1[k - 1] : 0.f;
+        const float a = sh0 ? a1 : a0;
+        const float c = sh1 ? c1 : c0;
+        S0[k] = a;
+        DS[k] = c - a;
+    }
     return min(b0, b1);
 }
 
@@ -345,7 +336,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
             for (int a = 0; a < KW - 1; ++a) {
                 cum += DSz[a] * tx;
-                if (Acc::kAll || cum != 0.f) acc.add(0, bz + a, bx + b, 0, f1 * cum);
+                if (cum != 0.f) acc.add(0, bz + a, bx + b, 0, f1 * cum);
             }
         }
 #pragma unroll
@@ -356,11 +347,11 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
             for (int b = 0; b < KW; ++b) {
                 if (b < KW - 1) {
                     cum += DSx[b] * tz;
-                    if (Acc::kAll || cum != 0.f) acc.add(1, bz + a, bx + b, 0, f2 * cum);
+                    if (cum != 0.f) acc.add(1, bz + a, bx + b, 0, f2 * cum);
                 }
                 float w3 = S0z[a] * S0x[b] + 0.5f * DSz[a] * S0x[b] + 0.5f * S0z[a] * DSx[b]
                          + (1.f / 3.f) * DSz[a] * DSx[b];
-                if (Acc::kAll || w3 != 0.f) acc.add(2, bz + a, bx + b, 0, qv * v3 * w3);
+                if (w3 != 0.f) acc.add(2, bz + a, bx + b, 0, qv * v3 * w3);
             }
         }
     } else {
@@ -375,7 +366,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
                 for (int a = 0; a < KW - 1; ++a) {
                     cum += DSz[a] * t;
-                    if (Acc::kAll || cum != 0.f) acc.add(0, bz + a, bx + b, by + c, f1 * cum);
+                    if (cum != 0.f) acc.add(0, bz + a, bx + b, by + c, f1 * cum);
                 }
             }
 #pragma unroll
@@ -388,7 +379,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
                 for (int b = 0; b < KW - 1; ++b) {
                     cum += DSx[b] * t;
-                    if (Acc::kAll || cum != 0.f) acc.add(1, bz + a, bx + b, by + c, f2 * cum);
+                    if (cum != 0.f) acc.add(1, bz + a, bx + b, by + c, f2 * cum);
                 }
             }
 #pragma unroll
@@ -399,7 +390,7 @@ __device__ __forceinline__ void deposit(const GridP& g, float qv, float v3, cons
 #pragma unroll
                 for (int c = 0; c < KW - 1; ++c) {
                     cum += DSy[c] * t;
-                    if (Acc::kAll || cum != 0.f) acc.add(2, bz + a, bx + b, by + c, f3 * cum);
+                    if (cum != 0.f) acc.add(2, bz + a, bx + b, by + c, f3 * cum);
                 }
             }
         }
@@ -437,12 +428,12 @@ __device__ __forceinline__ bool advance_one(const GridP& g, const SpeciesP& sp, 
     gather<NDIM, SHAPE>(g, E, B, p0, eb);
     boris(sp.eps, eb, u);
 
-    float gh, gl;
-    gamma_ff(u, gh, gl);
+    float gh, gl, rg;
+    gamma_ff(u, gh, gl, rg);
     float dzh, dzl, dxh, dxl, dyh = 0.f, dyl = 0.f;
-    displacement(u[0], gh, gl, sp.kz[0], sp.kz[1], dzh, dzl);
-    displacement(u[1], gh, gl, sp.kx[0], sp.kx[1], dxh, dxl);
-    if (NDIM == 3) displacement(u[2], gh, gl, sp.ky[0], sp.ky[1], dyh, dyl);
+    displacement(u[0], gh, gl, rg, sp.kz[0], sp.kz[1], dzh, dzl);
+    displacement(u[1], gh, gl, rg, sp.kx[0], sp.kx[1], dxh, dxl);
+    if (NDIM == 3) displacement(u[2], gh, gl, rg, sp.ky[0], sp.ky[1], dyh, dyl);
     // |v| < c and dt below the stability limit keep every move under one cell; anything else
     // (a non-finite field or momentum) retires the particle instead of indexing outside.
     if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f && fabsf(dyh) < 1.f)) {
@@ -454,7 +445,7 @@ __device__ __forceinline__ bool advance_one(const GridP& g, const SpeciesP& sp, 
     advance_axis(p1.iz, p1.oz, dzh, dzl);
     advance_axis(p1.ix, p1.ox, dxh, dxl);
     if (NDIM == 3) advance_axis(p1.iy, p1.oy, dyh, dyl);
-    v3 = u[2] / gh;
+    v3 = u[2] * rg;
 
     int wx = wrapi(p1.ix, g.nx);
     int wy = NDIM == 3 ? wrapi(p1.iy, g.ny) : 0;
@@ -490,115 +481,8 @@ __global__ void __launch_bounds__(256) push_kernel(GridP g, SpeciesP sp, const f
     }
 }
 
-// Shared-memory current box of the fused kernel: 3 components, at most BOX_CAP floats.
+// Particles per chunk of the fused kernels (one per thread).
 constexpr int FUSED_T = 256;
-constexpr int BOX_CAP = 12288;
-
-// Gather + Boris + move + Esirkepov deposition, fused.  Each CTA takes chunks of FUSED_T
-// consecutive particles (cell-sorted, so a chunk covers a compact patch of cells); the chunk's
-// currents are accumulated in a shared-memory box spanning its deposition windows and then
-// added to J once per non-zero node.  A chunk whose box exceeds BOX_CAP (unsorted particles,
-// a chunk across the periodic seam) deposits straight to global memory.
-template <int NDIM, int SHAPE>
-__device__ __forceinline__ void push_deposit_chunks(const GridP& g, const SpeciesP& sp, const float* __restrict__ E,
-                                                    const float* __restrict__ B, float* __restrict__ J, int shift,
-                                                    long long chunk0, long long nchunk_stride, float* sJ, int* box) {
-    constexpr int KW = Shape<SHAPE>::K + 1;
-    const long long n = *sp.count;
-    const long long cap = sp.cap;
-    const int lane = threadIdx.x & 31;
-    for (long long base = chunk0 * FUSED_T; base < n; base += nchunk_stride * FUSED_T) {
-        if (threadIdx.x < 6) box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
-        __syncthreads();
-        const long long p = base + threadIdx.x;
-        Pos p0, p1;
-        float v3 = 0.f;
-        bool ok = p < n && advance_one<NDIM, SHAPE, MODE_FUSED>(g, sp, E, B, shift, p, cap, p0, p1, v3);
-        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-        if (ok) {
-            lo[0] = window_base<SHAPE>(p0.iz, p0.oz, p1.iz, p1.oz);
-            lo[1] = window_base<SHAPE>(p0.ix, p0.ox, p1.ix, p1.ox);
-            lo[2] = NDIM == 3 ? window_base<SHAPE>(p0.iy, p0.oy, p1.iy, p1.oy) : 0;
-            hi[0] = lo[0] + KW - 1;
-            hi[1] = lo[1] + KW - 1;
-            hi[2] = NDIM == 3 ? lo[2] + KW - 1 : 0;
-        }
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            int mn = __reduce_min_sync(0xffffffffu, lo[a]);
-            int mx = __reduce_max_sync(0xffffffffu, hi[a]);
-            if (lane == 0 && mn != INT_MAX) {
-                atomicMin(&box[2 * a], mn);
-                atomicMax(&box[2 * a + 1], mx);
-            }
-        }
-        __syncthreads();
-        const bool any = box[0] != INT_MAX;
-        const int zl = any ? box[1] - box[0] + 1 : 0;
-        const int xl = any ? box[3] - box[2] + 1 : 0;
-        const int yl = any ? box[5] - box[4] + 1 : 0;
-        const long long vol = (long long)zl * xl * yl;
-        if (any && 3 * vol <= BOX_CAP) {
-            const int v = (int)vol;
-            for (int i = threadIdx.x; i < 3 * v; i += FUSED_T) sJ[i] = 0.f;
-            __syncthreads();
-            SharedAcc acc{sJ, box[0], box[2], box[4], zl, xl, v};
-            // one window for the whole warp (all lanes live, same window origin): warp-sum first
-            const unsigned live = __ballot_sync(0xffffffffu, ok);
-            // exact key: window origins are >= -2 and below 2^20 - 4 on every axis
-            unsigned long long key = ok ? (((unsigned long long)(lo[0] + 4) << 40) |
-                                           ((unsigned long long)(lo[1] + 4) << 20) |
-                                           (unsigned long long)(lo[2] + 4))
-                                        : ~0ull;
-            int same = 0;
-            __match_all_sync(0xffffffffu, key, &same);
-            if (live == 0xffffffffu && same) {
-                WarpSharedAcc wacc{acc, lane == 0};
-                deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, wacc);
-            } else if (ok) {
-                deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, acc);
-            }
-            __syncthreads();
-            // flush: one warp per z row of the box, lanes along z
-            const int rows = 3 * yl * xl;
-            for (int r = threadIdx.x >> 5; r < rows; r += FUSED_T >> 5) {
-                const int c = r / (yl * xl), q = r - c * (yl * xl);
-                const int y = q / xl, x = q - y * xl;
-                const int rowoff = c * (int)g.ncell + (wrapi(box[4] + y, g.ny) * g.nx + wrapi(box[2] + x, g.nx)) * g.nz;
-                const float* src = sJ + c * v + q * zl;
-                for (int z = lane; z < zl; z += 32) {
-                    float val = src[z];
-                    int gz = box[0] + z;
-                    if (val != 0.f && (unsigned)gz < (unsigned)g.nz) atomicAdd(J + rowoff + gz, val);
-                }
-            }
-        } else if (ok) {
-            GlobalAcc acc{&g, J};
-            deposit<NDIM, SHAPE>(g, sp.qv, v3, p0, p1, acc);
-        }
-        __syncthreads();
-    }
-}
-
-template <int NDIM, int SHAPE>
-__global__ void __launch_bounds__(FUSED_T, NDIM == 3 ? 2 : 4) push_deposit_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
-                                                               const float* __restrict__ B, float* __restrict__ J,
-                                                               int shift) {
-    extern __shared__ float sJ[];
-    __shared__ int box[6];
-    push_deposit_chunks<NDIM, SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, sJ, box);
-}
-
-// Many independent runs: blockIdx.y selects the instance, blockIdx.x strides over its chunks.
-template <int NDIM, int SHAPE>
-__global__ void __launch_bounds__(FUSED_T, NDIM == 3 ? 2 : 4) push_deposit_batch_kernel(const PartInst* __restrict__ inst,
-                                                                                        int parity) {
-    extern __shared__ float sJ[];
-    __shared__ int box[6];
-    const PartInst& q = inst[blockIdx.y];
-    const GridP g = prep_device(q.g);
-    push_deposit_chunks<NDIM, SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, sJ, box);
-}
 
 // ---------------------------------------------------------------- 2D fused kernel ----
 // Specialised 2D gather + push + Esirkepov for cell-sorted particles.  Per chunk of FUSED_T
@@ -615,18 +499,19 @@ __global__ void __launch_bounds__(FUSED_T, NDIM == 3 ? 2 : 4) push_deposit_batch
 // Boxes larger than the shared-memory caps fall back to global loads / global atomics.
 constexpr int F_CAP = 6 * 1536;    // field box floats (6 components)
 constexpr int J_CAP = 3 * 1536;    // current box floats (3 components)
-constexpr int DIRECT_STEPS = 2;    // runs of up to 4 lanes deposit without the warp reduction
 
 // floor(i / d) for 0 <= i < 2^22 from r = 1/d rounded to nearest: (i + 1/2) r is within
 // (i + 1/2) 2^-23 / d of (i + 1/2) / d, which lies at least 1/(2d) from an integer.
 __device__ __forceinline__ int box_div(int i, float r) { return (int)(((float)i + 0.5f) * r); }
 
+// Runs of consecutive lanes with the same deposition window (cell-sorted particles of a dense
+// beam): a segmented warp sum lets only the first lane of each run add the run's total.
 struct SegReduce {
     bool same[5];       // lane + 2^k belongs to the same run
     bool head;          // first lane of its run: adds the run's total
     int steps;          // warp-uniform: ceil(log2(longest run)), 0 when no lanes share a window
-    __device__ __forceinline__ float sum(float v) const {
-        float t;
+    __device__ __forceinline__ int sum(int v) const {
+        int t;
         if (steps > 0) { t = __shfl_down_sync(0xffffffffu, v, 1);  if (same[0]) v += t; }
         if (steps > 1) { t = __shfl_down_sync(0xffffffffu, v, 2);  if (same[1]) v += t; }
         if (steps > 2) { t = __shfl_down_sync(0xffffffffu, v, 4);  if (same[2]) v += t; }
@@ -670,22 +555,60 @@ __device__ __forceinline__ void box_reduce(int* box, int lz, int hz, int lx, int
     }
 }
 
-// K x K interpolation from a shared-memory box (rows of length zl along z)
+// Field box of a chunk, rows of fzl (a multiple of 4) floats along z, fvol = fxl fzl nodes:
+//   P1[fvol] float2 = (E1, B2): half cell along z, node along x  -> weights (Wzh, Wxn)
+//   P2[fvol] float2 = (E2, B1): node along z, half cell along x  -> weights (Wzn, Wxh)
+//   S3[fvol] = E3 (node, node),  T3[fvol] = B3 (half, half)
+// Components that share a stencil are interpolated together with packed FP32 FMAs.
 template <int K>
-__device__ __forceinline__ float tile_interp(const float* __restrict__ f, int zl, int z, int x, const float (&Wz)[K],
-                                             const float (&Wx)[K]) {
-    const float* r = f + x * zl + z;
-    float acc = 0.f;
+__device__ __forceinline__ float2 tile_interp2(const float2* __restrict__ f, int zl, int z, int x, const float (&Wz)[K],
+                                               const float (&Wx)[K]) {
+    const float2* r = f + x * zl + z;
+    float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
     for (int b = 0; b < K; ++b) {
-        float t = 0.f;
+        float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < K; ++a) t = fmaf(Wz[a], r[a], t);
-        acc = fmaf(Wx[b], t, acc);
+        for (int a = 0; a < K; ++a) t = __ffma2_rn(make_float2(Wz[a], Wz[a]), r[a], t);
+        acc = __ffma2_rn(make_float2(Wx[b], Wx[b]), t, acc);
         r += zl;
     }
     return acc;
 }
+
+// E3 and B3 (different stencils) as one packed chain: .x = E3, .y = B3.
+template <int K>
+__device__ __forceinline__ float2 tile_interp_e3b3(const float* __restrict__ S3, const float* __restrict__ T3, int zl,
+                                                   int za, int xa, int zb, int xb, const float (&Wza)[K],
+                                                   const float (&Wxa)[K], const float (&Wzb)[K],
+                                                   const float (&Wxb)[K]) {
+    const float* r = S3 + xa * zl + za;
+    const float* q = T3 + xb * zl + zb;
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+        float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int a = 0; a < K; ++a) t = __ffma2_rn(make_float2(Wza[a], Wzb[a]), make_float2(r[a], q[a]), t);
+        acc = __ffma2_rn(make_float2(Wxa[b], Wxb[b]), t, acc);
+        r += zl;
+        q += zl;
+    }
+    return acc;
+}
+
+// Cells gz..gz+3 of a field row into a (zero outside 0 <= z < nz); vec: 16-byte groups.
+__device__ __forceinline__ float4 load_group(const float* __restrict__ row, int gz, int nz, bool vec) {
+    if (vec && gz >= 0 && gz + 3 < nz) return __ldg(reinterpret_cast<const float4*>(row + gz));
+    float4 a;
+    a.x = (unsigned)gz < (unsigned)nz ? __ldg(row + gz) : 0.f;
+    a.y = (unsigned)(gz + 1) < (unsigned)nz ? __ldg(row + gz + 1) : 0.f;
+    a.z = (unsigned)(gz + 2) < (unsigned)nz ? __ldg(row + gz + 2) : 0.f;
+    a.w = (unsigned)(gz + 3) < (unsigned)nz ? __ldg(row + gz + 3) : 0.f;
+    return a;
+}
+
+__device__ __forceinline__ bool aligned16(const void* q) { return ((uintptr_t)q & 15) == 0; }
 
 template <int SHAPE>
 __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const SpeciesP& sp,
@@ -697,8 +620,10 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
     const long long n = *sp.count;
     const long long cap = sp.cap;
     const int N = (int)g.ncell;
+    const bool fvec = (g.nz & 3) == 0 && aligned16(E) && aligned16(B);
+    const bool jvec = (g.nz & 3) == 0 && aligned16(J);
     for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T) {
-        if (threadIdx.x < 8) box[threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        if (threadIdx.x < 5) box[threadIdx.x] = threadIdx.x == 4 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
         __syncthreads();
         const long long p = base + threadIdx.x;
         // ---- load and decode ----
@@ -724,7 +649,7 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
                 }
             }
         }
-        // ---- gather weights and the chunk's field box ----
+        // ---- gather weights and the chunk's boxes ----
         float Wzn[K], Wzh[K], Wxn[K], Wxh[K];
         int bzn = 0, bzh = 0, bxn = 0, bxh = 0;
         if (ok) {
@@ -737,31 +662,62 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
                    ok ? min(bxn, bxh) : INT_MAX, ok ? max(bxn, bxh) + K - 1 : INT_MIN);
         __syncthreads();
         const bool any = box[0] != INT_MAX;
-        const int fz0 = box[0], fx0 = box[2];
-        const int fzl = any ? box[1] - box[0] + 1 : 0, fxl = any ? box[3] - box[2] + 1 : 0;
+        // field box: z aligned down to a multiple of 4, rows padded to whole groups
+        const int fz0 = any ? (box[0] & ~3) : 0, fx0 = box[2];
+        const int fzl = any ? ((box[1] + 1 - fz0 + 3) & ~3) : 0, fxl = any ? box[3] - box[2] + 1 : 0;
         const int fvol = fzl * fxl;
         const bool ftile = any && 6 * fvol <= F_CAP && fxl <= g.nx + 2 * K;
+        // current box: every deposition window lies within one node below and two above the
+        // gather stencils (the move is under one cell per axis)
+        const int jz0 = any ? ((box[0] - 1) & ~3) : 0, jx0 = box[2] - 1;
+        const int jzl = any ? ((box[1] + 3 - jz0 + 3) & ~3) : 0, jxl = any ? box[3] - box[2] + 4 : 0;
+        const int jvol = jzl * jxl;
+        const bool jtile = any && 3 * jvol <= J_CAP && jxl <= g.nx + 2 * KW;
+        float2* P1 = reinterpret_cast<float2*>(sF);
+        float2* P2 = P1 + fvol;
+        float* S3 = sF + 4 * fvol;
+        float* T3 = S3 + fvol;
         if (ftile) {
-            // one box float per thread and pass: i = (c fxl + x) fzl + z
-            const float rv = 1.f / (float)fvol, rz = 1.f / (float)fzl;
-            for (int i = threadIdx.x; i < 6 * fvol; i += FUSED_T) {
-                const int c = box_div(i, rv), rem = i - c * fvol;
-                const int x = box_div(rem, rz), gz = fz0 + rem - x * fzl;
-                const float* src = (c < 3 ? E + c * N : B + (c - 3) * N) + wrapi(fx0 + x, g.nx) * g.nz;
-                sF[i] = ((unsigned)gz < (unsigned)g.nz) ? __ldg(src + gz) : 0.f;
+            const int ng = fzl >> 2;
+            const float rg = 1.f / (float)ng, rx = 1.f / (float)fxl;
+            for (int i = threadIdx.x; i < 3 * fxl * ng; i += FUSED_T) {
+                const int r = box_div(i, rg), zg = i - r * ng;
+                const int pc = box_div(r, rx), x = r - pc * fxl;
+                const long long row = (long long)wrapi(fx0 + x, g.nx) * g.nz;
+                const int gz = fz0 + 4 * zg;
+                const int o = x * fzl + 4 * zg;
+                // pc = 0: (E1, B2), 1: (E2, B1), 2: E3, B3
+                const float* fa = E + pc * N + row;
+                const float* fb = B + (pc == 0 ? N : pc == 1 ? 0 : 2 * N) + row;
+                const float4 a = load_group(fa, gz, g.nz, fvec), b = load_group(fb, gz, g.nz, fvec);
+                if (pc < 2) {
+                    float4* d = reinterpret_cast<float4*>((pc == 0 ? P1 : P2) + o);
+                    d[0] = make_float4(a.x, b.x, a.y, b.y);
+                    d[1] = make_float4(a.z, b.z, a.w, b.w);
+                } else {
+                    *reinterpret_cast<float4*>(S3 + o) = a;
+                    *reinterpret_cast<float4*>(T3 + o) = b;
+                }
             }
         }
+        if (jtile)
+            for (int i = threadIdx.x; i < (3 * jvol) >> 2; i += FUSED_T)
+                reinterpret_cast<float4*>(sJ)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         // ---- gather (staggering: E1 z+, E2 x+, E3 node, B1 x+, B2 z+, B3 z+ x+) ----
         float eb[6];
         if (ok) {
             if (ftile) {
-                eb[0] = tile_interp<K>(sF + 0 * fvol, fzl, bzh - fz0, bxn - fx0, Wzh, Wxn);
-                eb[1] = tile_interp<K>(sF + 1 * fvol, fzl, bzn - fz0, bxh - fx0, Wzn, Wxh);
-                eb[2] = tile_interp<K>(sF + 2 * fvol, fzl, bzn - fz0, bxn - fx0, Wzn, Wxn);
-                eb[3] = tile_interp<K>(sF + 3 * fvol, fzl, bzn - fz0, bxh - fx0, Wzn, Wxh);
-                eb[4] = tile_interp<K>(sF + 4 * fvol, fzl, bzh - fz0, bxn - fx0, Wzh, Wxn);
-                eb[5] = tile_interp<K>(sF + 5 * fvol, fzl, bzh - fz0, bxh - fx0, Wzh, Wxh);
+                const float2 q1 = tile_interp2<K>(P1, fzl, bzh - fz0, bxn - fx0, Wzh, Wxn);
+                const float2 q2 = tile_interp2<K>(P2, fzl, bzn - fz0, bxh - fx0, Wzn, Wxh);
+                const float2 q3 = tile_interp_e3b3<K>(S3, T3, fzl, bzn - fz0, bxn - fx0, bzh - fz0, bxh - fx0, Wzn,
+                                                      Wxn, Wzh, Wxh);
+                eb[0] = q1.x;
+                eb[4] = q1.y;
+                eb[1] = q2.x;
+                eb[3] = q2.y;
+                eb[2] = q3.x;
+                eb[5] = q3.y;
             } else {
                 gather<2, SHAPE>(g, E, B, p0, eb);
             }
@@ -771,18 +727,18 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
         float v3 = 0.f;
         if (ok) {
             boris(sp.eps, eb, u);
-            float gh, gl;
-            gamma_ff(u, gh, gl);
+            float gh, gl, rg;
+            gamma_ff(u, gh, gl, rg);
             float dzh, dzl, dxh, dxl;
-            displacement(u[0], gh, gl, sp.kz[0], sp.kz[1], dzh, dzl);
-            displacement(u[1], gh, gl, sp.kx[0], sp.kx[1], dxh, dxl);
+            displacement(u[0], gh, gl, rg, sp.kz[0], sp.kz[1], dzh, dzl);
+            displacement(u[1], gh, gl, rg, sp.kx[0], sp.kx[1], dxh, dxl);
             if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f)) {
                 ok = false;
                 sp.cell[p] = -1;
             } else {
                 advance_axis(p1.iz, p1.oz, dzh, dzl);
                 advance_axis(p1.ix, p1.ox, dxh, dxl);
-                v3 = u[2] / gh;
+                v3 = u[2] * rg;
                 const int wx = wrapi(p1.ix, g.nx);
                 sp.cell[p] = (p1.iz >= 0 && p1.iz < g.nz) ? encode(g, p1.iz, wx, 0) : -1;
                 sp.off[p] = p1.oz;
@@ -792,104 +748,431 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
                 sp.u[2 * cap + p] = u[2];
             }
         }
-        // ---- deposition vectors ----
+        // ---- deposition ----
         float S0z[KW], DSz[KW], S0x[KW], DSx[KW];
         int bz = 0, bx = 0;
         if (ok) {
-            bz = axis_weights<SHAPE>(p0.iz, p0.oz, p1.iz, p1.oz, S0z, DSz);
-            bx = axis_weights<SHAPE>(p0.ix, p0.ox, p1.ix, p1.ox, S0x, DSx);
+            bz = axis_weights_from<SHAPE>(bzn, Wzn, p1.iz, p1.oz, S0z, DSz);
+            bx = axis_weights_from<SHAPE>(bxn, Wxn, p1.ix, p1.ox, S0x, DSx);
         } else {
 #pragma unroll
             for (int k = 0; k < KW; ++k) S0z[k] = DSz[k] = S0x[k] = DSx[k] = 0.f;
         }
-        if (threadIdx.x < 4) box[4 + threadIdx.x] = (threadIdx.x & 1) ? INT_MIN : INT_MAX;
-        __syncthreads();
-        box_reduce(box + 4, ok ? bz : INT_MAX, ok ? bz + KW - 1 : INT_MIN, ok ? bx : INT_MAX, ok ? bx + KW - 1 : INT_MIN);
-        __syncthreads();
-        const int jz0 = box[4], jx0 = box[6];
-        const bool jany = jz0 != INT_MAX;
-        const int jzl = jany ? box[5] - jz0 + 1 : 0, jxl = jany ? box[7] - jx0 + 1 : 0;
-        const int jvol = jzl * jxl;
-        const bool jtile = jany && 3 * jvol <= J_CAP && jxl <= g.nx + 2 * KW;
-        if (jtile)
-            for (int i = threadIdx.x; i < 3 * jvol; i += FUSED_T) sJ[i] = 0.f;
-        __syncthreads();
-        if (jany) {
-            // runs of lanes with the same window
-            const unsigned long long key = ok ? (((unsigned long long)(bz + 4) << 32) | (unsigned)(bx + 4))
-                                              : (0xFFFFFFFF00000000ull | (unsigned)threadIdx.x);
-            const SegReduce seg = make_segments(key);
-            const float f1 = -sp.qv * g.dz / g.dt, f2 = -sp.qv * g.dx / g.dt, f3 = sp.qv * v3;
-            float Cz[KW], Tz[KW], Cx[KW], Tx[KW], Ax[KW], Bx[KW];
-            float cz = 0.f, cx = 0.f;
+        // J1(a,b) = Cz[a] Tx[b], J2(a,b) = Tz[a] Cx[b], J3(a,b) = S0z[a] Ax[b] + DSz[a] Bx[b] with
+        // Cz = f1 cumsum dSz, Cx = f2 cumsum dSx, T = S0 + dS/2, Ax = f3 Tx, Bx = f3 (S0x/2 + dSx/3).
+        const float f1 = -sp.qv * g.dz / g.dt, f2 = -sp.qv * g.dx / g.dt, f3 = sp.qv * v3;
+        float cz[KW], cx[KW];
+        float mb = fabsf(f3);         // bound of every contribution of this particle (below)
+        {
+            float az = 0.f, ax = 0.f;
 #pragma unroll
             for (int k = 0; k < KW; ++k) {
-                cz += DSz[k];
-                cx += DSx[k];
-                Cz[k] = f1 * cz;
-                Cx[k] = f2 * cx;
-                Tz[k] = S0z[k] + 0.5f * DSz[k];
-                Tx[k] = S0x[k] + 0.5f * DSx[k];
-                Ax[k] = f3 * Tx[k];                                   // S0x + dSx/2
-                Bx[k] = f3 * (0.5f * S0x[k] + (1.f / 3.f) * DSx[k]);
+                az += DSz[k];
+                ax += DSx[k];
+                cz[k] = az;
+                cx[k] = ax;
+                mb = fmaxf(mb, fmaxf(fabsf(f1 * az), fabsf(f2 * ax)));
             }
-            // shared box: the lane's window origin in the box; global fallback: wrapped row offsets
-            const int sbase = (bx - jx0) * jzl + (bz - jz0);
-            if (jtile && seg.steps <= DIRECT_STEPS) {
-                // short runs (at most 2^DIRECT_STEPS lanes on one node): every live lane adds its
-                // own values; the few-way address conflicts cost less than the reduction
-                float* s0 = sJ + sbase;
+        }
+        // The shared current box accumulates in 32-bit fixed point: integer shared atomics are
+        // single instructions, where FP32 ones retry on every conflicting lane, and integer sums
+        // reduce across a warp in one instruction.  Tz, Tx and the 2D J3 weight
+        // (S0z S0x + S1z S1x)/3 + (S0z S1x + S1z S0x)/6 lie in [0, 1], so no contribution
+        // exceeds mb = max(|Cz|, |Cx|, |f3|).  With 2^(e-1) <= max mb < 2^e over the chunk, the
+        // scale s = 2^(22-e) keeps every scaled contribution (and each of the two products of
+        // J3) below 2^22, where adding 1.5 2^23 rounds it to an integer in the low mantissa
+        // bits, and every node sum of at most FUSED_T particles below 2^30.  The rounding step
+        // is below 2^-21 of the chunk's largest contribution.
+        if (jtile) {
+            const unsigned wm = __reduce_max_sync(0xffffffffu, ok ? __float_as_uint(mb) : 0u);
+            if ((threadIdx.x & 31) == 0 && wm) atomicMax(reinterpret_cast<unsigned*>(box + 4), wm);
+        }
+        __syncthreads();
+        const int mbits = box[4];
+        const int sexp = min(275 - (mbits >> 23), 253);       // biased exponent of s
+        const float fs = __int_as_float(sexp << 23), inv_s = __int_as_float((254 - sexp) << 23);
+        int* const iJ = reinterpret_cast<int*>(sJ);
+        if (any && jtile && mbits != 0) {
+            const float g1 = f1 * fs, g2 = f2 * fs, g3 = f3 * fs;
+            float2 CT[KW], TC[KW];        // (s Cz, Tz)[a], (Tx, s Cx)[b]
+            float Ax[KW], Bx[KW];         // s Ax, s Bx
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                CT[k] = make_float2(g1 * cz[k], S0z[k] + 0.5f * DSz[k]);
+                const float tx = S0x[k] + 0.5f * DSx[k];
+                TC[k] = make_float2(tx, g2 * cx[k]);
+                Ax[k] = g3 * tx;
+                Bx[k] = g3 * (0.5f * S0x[k] + (1.f / 3.f) * DSx[k]);
+            }
+            // Lanes sharing a window hit the same nodes.  With at most 4 lanes per window anywhere
+            // in the warp every live lane adds its own values (at most 4-way address conflicts);
+            // otherwise (dense beams) runs of consecutive lanes are summed first and one lane per
+            // run adds the total.  Empty slots have unique keys.
+            const unsigned long long key = ok ? (((unsigned long long)(bz + 4) << 32) | (unsigned)(bx + 4))
+                                              : (0xFFFFFFFF00000000ull | (unsigned)threadIdx.x);
+            const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
+            int* s0 = iJ + (bx - jx0) * jzl + (bz - jz0);
+            const float MAGIC = 12582912.f;           // 1.5 2^23
+            auto terms = [&](auto&& put) {
 #pragma unroll
                 for (int b = 0; b < KW; ++b)
 #pragma unroll
                     for (int a = 0; a < KW; ++a) {
-                        float v;
-                        if (a < KW - 1) {
-                            v = Cz[a] * Tx[b];
-                            if (ok && v != 0.f) atomicAdd(s0 + b * jzl + a, v);
+                        const int o = b * jzl + a;
+                        if (a < KW - 1 && b < KW - 1) {
+                            const float2 v = __ffma2_rn(CT[a], TC[b], make_float2(MAGIC, MAGIC));
+                            put(o, v.x);
+                            put(jvol + o, v.y);
+                        } else if (a < KW - 1) {
+                            put(o, fmaf(CT[a].x, TC[b].x, MAGIC));
+                        } else if (b < KW - 1) {
+                            put(jvol + o, fmaf(CT[a].y, TC[b].y, MAGIC));
                         }
-                        if (b < KW - 1) {
-                            v = Tz[a] * Cx[b];
-                            if (ok && v != 0.f) atomicAdd(s0 + jvol + b * jzl + a, v);
-                        }
-                        v = S0z[a] * Ax[b] + DSz[a] * Bx[b];
-                        if (ok && v != 0.f) atomicAdd(s0 + 2 * jvol + b * jzl + a, v);
+                        put(2 * jvol + o, fmaf(S0z[a], Ax[b], fmaf(DSz[a], Bx[b], MAGIC)));
                     }
+            };
+            if (gmax <= 4) {
+                if (ok) terms([&](int o, float biased) { atomicAdd(s0 + o, __float_as_int(biased) - 0x4B400000); });
             } else {
-                int grow[KW];
+                const SegReduce seg = make_segments(key);
+                terms([&](int o, float biased) {
+                    const int v = seg.sum(__float_as_int(biased) - 0x4B400000);
+                    if (seg.head && ok && v != 0) atomicAdd(s0 + o, v);
+                });
+            }
+        } else if (any && !jtile && ok) {
+            // box too large for shared memory: FP32 atomics straight to J
 #pragma unroll
-                for (int b = 0; b < KW; ++b) grow[b] = wrapi(bx + b, g.nx) * g.nz;
-                auto put = [&](int c, int a, int b, float v) {
-                    v = seg.sum(v);
-                    // only live lanes own a window inside the box (dead or empty slots are one-lane
-                    // runs with no window; their sums are zero and they must not write)
-                    if (jtile) {
-                        if (seg.head && ok && v != 0.f) atomicAdd(sJ + c * jvol + sbase + b * jzl + a, v);
-                    } else {
-                        const int gz = bz + a;
-                        if (seg.head && ok && v != 0.f && (unsigned)gz < (unsigned)g.nz)
-                            atomicAdd(J + c * N + grow[b] + gz, v);
-                    }
-                };
+            for (int b = 0; b < KW; ++b) {
+                const int row = wrapi(bx + b, g.nx) * g.nz;
+                const float tx = S0x[b] + 0.5f * DSx[b];
+                const float ax = f3 * tx, bxv = f3 * (0.5f * S0x[b] + (1.f / 3.f) * DSx[b]);
 #pragma unroll
-                for (int b = 0; b < KW; ++b)
-#pragma unroll
-                    for (int a = 0; a < KW; ++a) {
-                        if (a < KW - 1) put(0, a, b, Cz[a] * Tx[b]);
-                        if (b < KW - 1) put(1, a, b, Tz[a] * Cx[b]);
-                        put(2, a, b, S0z[a] * Ax[b] + DSz[a] * Bx[b]);
-                    }
+                for (int a = 0; a < KW; ++a) {
+                    const int gz = bz + a;
+                    if ((unsigned)gz >= (unsigned)g.nz) continue;
+                    float* d = J + row + gz;
+                    float v;
+                    if (a < KW - 1 && (v = f1 * cz[a] * tx) != 0.f) atomicAdd(d, v);
+                    if (b < KW - 1 && (v = (S0z[a] + 0.5f * DSz[a]) * f2 * cx[b]) != 0.f) atomicAdd(d + N, v);
+                    if ((v = fmaf(S0z[a], ax, DSz[a] * bxv)) != 0.f) atomicAdd(d + 2 * N, v);
+                }
             }
         }
         __syncthreads();
+        if (jtile && mbits != 0) {
+            // box -> J in 16-byte groups (one vector atomic per group inside the grid)
+            const int ng = jzl >> 2;
+            const float rg = 1.f / (float)ng, rx = 1.f / (float)jxl;
+            for (int i = threadIdx.x; i < 3 * jxl * ng; i += FUSED_T) {
+                const int4 q = reinterpret_cast<const int4*>(iJ)[i];
+                if ((q.x | q.y | q.z | q.w) == 0) continue;
+                const float4 v = make_float4((float)q.x * inv_s, (float)q.y * inv_s, (float)q.z * inv_s,
+                                             (float)q.w * inv_s);
+                const int r = box_div(i, rg), zg = i - r * ng;
+                const int c = box_div(r, rx), x = r - c * jxl;
+                const int gz = jz0 + 4 * zg;
+                float* dst = J + c * N + wrapi(jx0 + x, g.nx) * g.nz + gz;
+                if (jvec && gz >= 0 && gz + 3 < g.nz) {
+                    atomicAdd(reinterpret_cast<float4*>(dst), v);
+                } else {
+                    if ((unsigned)gz < (unsigned)g.nz && q.x) atomicAdd(dst, v.x);
+                    if ((unsigned)(gz + 1) < (unsigned)g.nz && q.y) atomicAdd(dst + 1, v.y);
+                    if ((unsigned)(gz + 2) < (unsigned)g.nz && q.z) atomicAdd(dst + 2, v.z);
+                    if ((unsigned)(gz + 3) < (unsigned)g.nz && q.w) atomicAdd(dst + 3, v.w);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- 3D fused kernel ----
+// The 3D counterpart of push_deposit_2d_chunks: per chunk of FUSED_T cell-sorted particles the
+// gather footprint is staged in shared memory ([y][x][z] rows of whole 4-cell groups, one array
+// per component), components are interpolated in pairs with packed FP32 FMAs, and the 3D
+// Esirkepov current
+//   J1(a,b,c) = Cz[a] Txy(b,c), J2(a,b,c) = Cx[b] Tzy(a,c), J3(a,b,c) = Cy[c] Tzx(a,b),
+//   C_d = -(q w/V)(h_d/dt) cumsum dS_d,  T_uv = S0_u (S0_v + dS_v/2) + dS_u (S0_v/2 + dS_v/3)
+// is accumulated in a 32-bit fixed-point box as in 2D (T_uv lies in [0, 1], so |C_d| bounds
+// every contribution).
+constexpr int F_CAP3 = 8192;       // 3D field box floats (6 components)
+constexpr int J_CAP3 = 9216;       // 3D current box ints (3 components)
+
+// .x = sum Wza Wxa Wya Fa, .y = sum Wzb Wxb Wyb Fb over K^3 nodes of [y][x][z] boxes (row fzl,
+// fxl rows per plane); (z, x, y) are the stencil origins in the box.
+template <int K>
+__device__ __forceinline__ float2 tile_interp3_pair(const float* __restrict__ Fa, int za, int xa, int ya,
+                                                    const float (&Wza)[K], const float (&Wxa)[K],
+                                                    const float (&Wya)[K], const float* __restrict__ Fb, int zb,
+                                                    int xb, int yb, const float (&Wzb)[K], const float (&Wxb)[K],
+                                                    const float (&Wyb)[K], int fzl, int fxl) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        float2 tc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const float* ra = Fa + ((ya + c) * fxl + xa + b) * fzl + za;
+            const float* rb = Fb + ((yb + c) * fxl + xb + b) * fzl + zb;
+            float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < K; ++a) t = __ffma2_rn(make_float2(Wza[a], Wzb[a]), make_float2(ra[a], rb[a]), t);
+            tc = __ffma2_rn(make_float2(Wxa[b], Wxb[b]), t, tc);
+        }
+        acc = __ffma2_rn(make_float2(Wya[c], Wyb[c]), tc, acc);
+    }
+    return acc;
+}
+
+template <int SHAPE>
+__device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const SpeciesP& sp,
+                                                       const float* __restrict__ E, const float* __restrict__ B,
+                                                       float* __restrict__ J, int shift, long long chunk0,
+                                                       long long stride, float* sF, float* sJ, int* box) {
+    constexpr int K = Shape<SHAPE>::K;
+    constexpr int KW = K + 1;
+    const long long n = *sp.count;
+    const long long cap = sp.cap;
+    const int N = (int)g.ncell;
+    const bool fvec = (g.nz & 3) == 0 && aligned16(E) && aligned16(B);
+    const bool jvec = (g.nz & 3) == 0 && aligned16(J);
+    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T) {
+        if (threadIdx.x < 7) box[threadIdx.x] = threadIdx.x == 6 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        __syncthreads();
+        const long long p = base + threadIdx.x;
+        // ---- load and decode ----
+        bool ok = false;
+        Pos p0;
+        float u[3] = {0.f, 0.f, 0.f};
+        if (p < n) {
+            int cell = sp.cell[p];
+            if (cell >= 0) {
+                int izg;
+                decode(g, cell, izg, p0.ix, p0.iy);
+                p0.iz = izg - 1 - shift;
+                if (p0.iz >= 0 && p0.iz < g.nz) {
+                    ok = true;
+                    p0.oz = sp.off[p];
+                    p0.ox = sp.off[cap + p];
+                    p0.oy = sp.off[2 * cap + p];
+                    u[0] = sp.u[p];
+                    u[1] = sp.u[cap + p];
+                    u[2] = sp.u[2 * cap + p];
+                } else {
+                    sp.cell[p] = -1;
+                }
+            }
+        }
+        // ---- gather weights and the chunk's boxes ----
+        float Wzn[K], Wzh[K], Wxn[K], Wxh[K], Wyn[K], Wyh[K];
+        int bzn = 0, bzh = 0, bxn = 0, bxh = 0, byn = 0, byh = 0;
+        if (ok) {
+            bzn = p0.iz + Shape<SHAPE>::w(p0.oz, Wzn);
+            bzh = half_weights<SHAPE>(p0.iz, p0.oz, Wzh);
+            bxn = p0.ix + Shape<SHAPE>::w(p0.ox, Wxn);
+            bxh = half_weights<SHAPE>(p0.ix, p0.ox, Wxh);
+            byn = p0.iy + Shape<SHAPE>::w(p0.oy, Wyn);
+            byh = half_weights<SHAPE>(p0.iy, p0.oy, Wyh);
+        }
+        box_reduce(box, ok ? min(bzn, bzh) : INT_MAX, ok ? max(bzn, bzh) + K - 1 : INT_MIN,
+                   ok ? min(bxn, bxh) : INT_MAX, ok ? max(bxn, bxh) + K - 1 : INT_MIN);
+        {
+            const int c = __reduce_min_sync(0xffffffffu, ok ? min(byn, byh) : INT_MAX);
+            const int d = __reduce_max_sync(0xffffffffu, ok ? max(byn, byh) + K - 1 : INT_MIN);
+            if ((threadIdx.x & 31) == 0 && c != INT_MAX) {
+                atomicMin(box + 4, c);
+                atomicMax(box + 5, d);
+            }
+        }
+        __syncthreads();
+        const bool any = box[0] != INT_MAX;
+        const int fz0 = any ? (box[0] & ~3) : 0, fx0 = box[2], fy0 = box[4];
+        const int fzl = any ? ((box[1] + 1 - fz0 + 3) & ~3) : 0;
+        const int fxl = any ? box[3] - box[2] + 1 : 0, fyl = any ? box[5] - box[4] + 1 : 0;
+        const int fvol = fzl * fxl * fyl;
+        const bool ftile = any && 6 * fvol <= F_CAP3 && fxl <= g.nx + 2 * K && fyl <= g.ny + 2 * K;
+        const int jz0 = any ? ((box[0] - 1) & ~3) : 0, jx0 = box[2] - 1, jy0 = box[4] - 1;
+        const int jzl = any ? ((box[1] + 3 - jz0 + 3) & ~3) : 0;
+        const int jxl = any ? box[3] - box[2] + 4 : 0, jyl = any ? box[5] - box[4] + 4 : 0;
+        const int jvol = jzl * jxl * jyl;
+        const bool jtile = any && 3 * jvol <= J_CAP3 && jxl <= g.nx + 2 * KW && jyl <= g.ny + 2 * KW;
+        if (ftile) {
+            const int ng = fzl >> 2, rows = fyl * fxl;
+            const float rg = 1.f / (float)ng, rr = 1.f / (float)rows, rx = 1.f / (float)fxl;
+            for (int i = threadIdx.x; i < 6 * rows * ng; i += FUSED_T) {
+                const int r = box_div(i, rg), zg = i - r * ng;
+                const int c = box_div(r, rr), q = r - c * rows;
+                const int y = box_div(q, rx), x = q - y * fxl;
+                const long long row =
+                    ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
+                const float* f = (c < 3 ? E + c * N : B + (c - 3) * N) + row;
+                *reinterpret_cast<float4*>(sF + c * fvol + q * fzl + 4 * zg) = load_group(f, fz0 + 4 * zg, g.nz, fvec);
+            }
+        }
+        if (jtile)
+            for (int i = threadIdx.x; i < (3 * jvol) >> 2; i += FUSED_T)
+                reinterpret_cast<float4*>(sJ)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        // ---- gather (E1 z+, E2 x+, E3 y+, B1 x+ y+, B2 z+ y+, B3 z+ x+) ----
+        float eb[6];
+        if (ok) {
+            if (ftile) {
+                const float* F = sF;
+                const float2 q1 = tile_interp3_pair<K>(F, bzh - fz0, bxn - fx0, byn - fy0, Wzh, Wxn, Wyn,
+                                                       F + 4 * fvol, bzh - fz0, bxn - fx0, byh - fy0, Wzh, Wxn,
+                                                       Wyh, fzl, fxl);                       // E1, B2
+                const float2 q2 = tile_interp3_pair<K>(F + fvol, bzn - fz0, bxh - fx0, byn - fy0, Wzn, Wxh, Wyn,
+                                                       F + 3 * fvol, bzn - fz0, bxh - fx0, byh - fy0, Wzn, Wxh,
+                                                       Wyh, fzl, fxl);                       // E2, B1
+                const float2 q3 = tile_interp3_pair<K>(F + 2 * fvol, bzn - fz0, bxn - fx0, byh - fy0, Wzn, Wxn,
+                                                       Wyh, F + 5 * fvol, bzh - fz0, bxh - fx0, byn - fy0, Wzh,
+                                                       Wxh, Wyn, fzl, fxl);                  // E3, B3
+                eb[0] = q1.x;
+                eb[4] = q1.y;
+                eb[1] = q2.x;
+                eb[3] = q2.y;
+                eb[2] = q3.x;
+                eb[5] = q3.y;
+            } else {
+                gather<3, SHAPE>(g, E, B, p0, eb);
+            }
+        }
+        // ---- push and move ----
+        Pos p1 = p0;
+        if (ok) {
+            boris(sp.eps, eb, u);
+            float gh, gl, rg;
+            gamma_ff(u, gh, gl, rg);
+            float dzh, dzl, dxh, dxl, dyh, dyl;
+            displacement(u[0], gh, gl, rg, sp.kz[0], sp.kz[1], dzh, dzl);
+            displacement(u[1], gh, gl, rg, sp.kx[0], sp.kx[1], dxh, dxl);
+            displacement(u[2], gh, gl, rg, sp.ky[0], sp.ky[1], dyh, dyl);
+            if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f && fabsf(dyh) < 1.f)) {
+                ok = false;
+                sp.cell[p] = -1;
+            } else {
+                advance_axis(p1.iz, p1.oz, dzh, dzl);
+                advance_axis(p1.ix, p1.ox, dxh, dxl);
+                advance_axis(p1.iy, p1.oy, dyh, dyl);
+                const int wx = wrapi(p1.ix, g.nx), wy = wrapi(p1.iy, g.ny);
+                sp.cell[p] = (p1.iz >= 0 && p1.iz < g.nz) ? encode(g, p1.iz, wx, wy) : -1;
+                sp.off[p] = p1.oz;
+                sp.off[cap + p] = p1.ox;
+                sp.off[2 * cap + p] = p1.oy;
+                sp.u[p] = u[0];
+                sp.u[cap + p] = u[1];
+                sp.u[2 * cap + p] = u[2];
+            }
+        }
+        // ---- deposition ----
+        float S0z[KW], DSz[KW], S0x[KW], DSx[KW], S0y[KW], DSy[KW];
+        int bz = 0, bx = 0, by = 0;
+        if (ok) {
+            bz = axis_weights_from<SHAPE>(bzn, Wzn, p1.iz, p1.oz, S0z, DSz);
+            bx = axis_weights_from<SHAPE>(bxn, Wxn, p1.ix, p1.ox, S0x, DSx);
+            by = axis_weights_from<SHAPE>(byn, Wyn, p1.iy, p1.oy, S0y, DSy);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KW; ++k) S0z[k] = DSz[k] = S0x[k] = DSx[k] = S0y[k] = DSy[k] = 0.f;
+        }
+        const float f1 = -sp.qv * g.dz / g.dt, f2 = -sp.qv * g.dx / g.dt, f3 = -sp.qv * g.dy / g.dt;
+        float cz[KW], cx[KW], cy[KW];
+        float mb = 0.f;
+        {
+            float az = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                az += DSz[k];
+                ax += DSx[k];
+                ay += DSy[k];
+                cz[k] = az;
+                cx[k] = ax;
+                cy[k] = ay;
+                mb = fmaxf(mb, fmaxf(fabsf(f1 * az), fmaxf(fabsf(f2 * ax), fabsf(f3 * ay))));
+            }
+        }
+        // fixed-point scale of the chunk (see push_deposit_2d_chunks): s = 2^(22-e), max mb < 2^e
         if (jtile) {
-            const float rv = 1.f / (float)jvol, rz = 1.f / (float)jzl;
-            for (int i = threadIdx.x; i < 3 * jvol; i += FUSED_T) {
-                const float val = sJ[i];
-                if (val == 0.f) continue;
-                const int c = box_div(i, rv), rem = i - c * jvol;
-                const int x = box_div(rem, rz), gz = jz0 + rem - x * jzl;
-                if ((unsigned)gz < (unsigned)g.nz) atomicAdd(J + c * N + wrapi(jx0 + x, g.nx) * g.nz + gz, val);
+            const unsigned wm = __reduce_max_sync(0xffffffffu, ok ? __float_as_uint(mb) : 0u);
+            if ((threadIdx.x & 31) == 0 && wm) atomicMax(reinterpret_cast<unsigned*>(box + 6), wm);
+        }
+        __syncthreads();
+        const int mbits = box[6];
+        const int sexp = min(275 - (mbits >> 23), 253);
+        const float fs = __int_as_float(sexp << 23), inv_s = __int_as_float((254 - sexp) << 23);
+        int* const iJ = reinterpret_cast<int*>(sJ);
+        if (any && jtile && mbits != 0) {
+            float Cz[KW], Cx[KW], Cy[KW], Px[KW], Qx[KW], Py[KW], Qy[KW];
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                Cz[k] = f1 * fs * cz[k];
+                Cx[k] = f2 * fs * cx[k];
+                Cy[k] = f3 * fs * cy[k];
+                Px[k] = S0x[k] + 0.5f * DSx[k];
+                Qx[k] = 0.5f * S0x[k] + (1.f / 3.f) * DSx[k];
+                Py[k] = S0y[k] + 0.5f * DSy[k];
+                Qy[k] = 0.5f * S0y[k] + (1.f / 3.f) * DSy[k];
+            }
+            // window origins are >= -2 and below 2^20 - 4 on every axis: an exact 64-bit key
+            const unsigned long long key =
+                ok ? (((unsigned long long)(bz + 4) << 40) | ((unsigned long long)(bx + 4) << 20) |
+                      (unsigned long long)(by + 4))
+                   : (0xFFFFF00000000000ull | (unsigned)threadIdx.x);
+            const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
+            int* s0 = iJ + ((by - jy0) * jxl + (bx - jx0)) * jzl + (bz - jz0);
+            const float MAGIC = 12582912.f;           // 1.5 2^23
+            auto terms = [&](auto&& put) {
+#pragma unroll
+                for (int c = 0; c < KW; ++c)
+#pragma unroll
+                    for (int b = 0; b < KW; ++b) {
+                        const float txy = fmaf(S0x[b], Py[c], DSx[b] * Qy[c]);
+#pragma unroll
+                        for (int a = 0; a < KW; ++a) {
+                            const int o = (c * jxl + b) * jzl + a;
+                            if (a < KW - 1) put(o, fmaf(Cz[a], txy, MAGIC));
+                            if (b < KW - 1) put(jvol + o, fmaf(Cx[b], fmaf(S0z[a], Py[c], DSz[a] * Qy[c]), MAGIC));
+                            if (c < KW - 1)
+                                put(2 * jvol + o, fmaf(Cy[c], fmaf(S0z[a], Px[b], DSz[a] * Qx[b]), MAGIC));
+                        }
+                    }
+            };
+            if (gmax <= 4) {
+                if (ok) terms([&](int o, float biased) { atomicAdd(s0 + o, __float_as_int(biased) - 0x4B400000); });
+            } else {
+                const SegReduce seg = make_segments(key);
+                terms([&](int o, float biased) {
+                    const int v = seg.sum(__float_as_int(biased) - 0x4B400000);
+                    if (seg.head && ok && v != 0) atomicAdd(s0 + o, v);
+                });
+            }
+        } else if (any && !jtile && ok) {
+            GlobalAcc acc{&g, J};
+            deposit<3, SHAPE>(g, sp.qv, 0.f, p0, p1, acc);
+        }
+        __syncthreads();
+        if (jtile && mbits != 0) {
+            const int ng = jzl >> 2, rows = jyl * jxl;
+            const float rg = 1.f / (float)ng, rr = 1.f / (float)rows, rx = 1.f / (float)jxl;
+            for (int i = threadIdx.x; i < 3 * rows * ng; i += FUSED_T) {
+                const int4 q = reinterpret_cast<const int4*>(iJ)[i];
+                if ((q.x | q.y | q.z | q.w) == 0) continue;
+                const float4 v = make_float4((float)q.x * inv_s, (float)q.y * inv_s, (float)q.z * inv_s,
+                                             (float)q.w * inv_s);
+                const int r = box_div(i, rg), zg = i - r * ng;
+                const int c = box_div(r, rr), qq = r - c * rows;
+                const int y = box_div(qq, rx), x = qq - y * jxl;
+                const int gz = jz0 + 4 * zg;
+                float* dst = J + c * N + (wrapi(jy0 + y, g.ny) * g.nx + wrapi(jx0 + x, g.nx)) * g.nz + gz;
+                if (jvec && gz >= 0 && gz + 3 < g.nz) {
+                    atomicAdd(reinterpret_cast<float4*>(dst), v);
+                } else {
+                    if ((unsigned)gz < (unsigned)g.nz && q.x) atomicAdd(dst, v.x);
+                    if ((unsigned)(gz + 1) < (unsigned)g.nz && q.y) atomicAdd(dst + 1, v.y);
+                    if ((unsigned)(gz + 2) < (unsigned)g.nz && q.z) atomicAdd(dst + 2, v.z);
+                    if ((unsigned)(gz + 3) < (unsigned)g.nz && q.w) atomicAdd(dst + 3, v.w);
+                }
             }
         }
         __syncthreads();
@@ -897,18 +1180,41 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
 }
 
 template <int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
+                                                                     const float* __restrict__ B, float* __restrict__ J,
+                                                                     int shift) {
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    __shared__ int box[7];
+    push_deposit_3d_chunks<SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + F_CAP3, box);
+}
+
+template <int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_batch_kernel(const PartInst* __restrict__ inst, int parity) {
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    __shared__ int box[7];
+    const PartInst& q = inst[blockIdx.y];
+    const GridP g = prep_device(q.g);
+    push_deposit_3d_chunks<SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem,
+                                  smem + F_CAP3, box);
+}
+
+template <int SHAPE>
 __global__ void __launch_bounds__(FUSED_T, 4) push_deposit_2d_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
                                                                      const float* __restrict__ B, float* __restrict__ J,
                                                                      int shift) {
-    extern __shared__ float smem[];
-    __shared__ int box[8];
+    extern __shared__ float4 smem4[];      // 16-byte aligned: the boxes are read and written as float4
+    float* smem = reinterpret_cast<float*>(smem4);
+    __shared__ int box[5];
     push_deposit_2d_chunks<SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + F_CAP, box);
 }
 
 template <int SHAPE>
 __global__ void __launch_bounds__(FUSED_T, 4) push_deposit_2d_batch_kernel(const PartInst* __restrict__ inst, int parity) {
-    extern __shared__ float smem[];
-    __shared__ int box[8];
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    __shared__ int box[5];
     const PartInst& q = inst[blockIdx.y];
     const GridP g = prep_device(q.g);
     push_deposit_2d_chunks<SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem, smem + F_CAP,
@@ -954,10 +1260,10 @@ __device__ __forceinline__ void deposit_one(const GridP& g, const SpeciesP& sp, 
     p1.ox = sp.off[cap + p];
     p1.oy = NDIM == 3 ? sp.off[2 * cap + p] : 0.f;
     float u[3] = {sp.u[p], sp.u[cap + p], sp.u[2 * cap + p]};
-    float gh, gl;
-    gamma_ff(u, gh, gl);
+    float gh, gl, rg;
+    gamma_ff(u, gh, gl, rg);
     GlobalAcc acc{&g, J};
-    deposit<NDIM, SHAPE>(g, sp.qv, u[2] / gh, p0, p1, acc);
+    deposit<NDIM, SHAPE>(g, sp.qv, u[2] * rg, p0, p1, acc);
     if (p1.iz < 0 || p1.iz >= g.nz) sp.cell[p] = -1;
 }
 
@@ -1209,15 +1515,15 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
             }
             k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift);
         } else if (mode == MODE_FUSED) {
-            auto k = push_deposit_kernel<ND, SH>;
+            auto k = push_deposit_3d_kernel<SH>;
+            const size_t smem = (F_CAP3 + J_CAP3) * sizeof(float);
             static bool configured = false;
             if (!configured) {
-                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     (int)(BOX_CAP * sizeof(float)));
+                cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
                 configured = true;
             }
-            k<<<pblocks(extent), FUSED_T, BOX_CAP * sizeof(float), s>>>(g, sp, E, B, J, shift);
+            k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift);
         } else {
             push_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, shift);
         }
@@ -1244,15 +1550,15 @@ cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int sha
             k<<<grid, FUSED_T, smem, s>>>(inst, parity);
             return cudaGetLastError();
         }
-        auto k = push_deposit_batch_kernel<ND, SH>;
+        auto k = push_deposit_3d_batch_kernel<SH>;
+        const size_t smem = (F_CAP3 + J_CAP3) * sizeof(float);
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(BOX_CAP * sizeof(float)));
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             configured = true;
         }
-        k<<<grid, FUSED_T, BOX_CAP * sizeof(float), s>>>(inst, parity);
+        k<<<grid, FUSED_T, smem, s>>>(inst, parity);
         return cudaGetLastError();
     });
 }
