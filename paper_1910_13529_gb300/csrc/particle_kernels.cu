@@ -497,8 +497,17 @@ constexpr int FUSED_T = 256;
 //     their contributions with a segmented warp reduction first, so that only one lane per run
 //     issues the shared-memory atomic (dense beams otherwise serialise on the same addresses).
 // Boxes larger than the shared-memory caps fall back to global loads / global atomics.
-constexpr int F_CAP = 6 * 1536;    // field box floats (6 components)
-constexpr int J_CAP = 3 * 1536;    // current box floats (3 components)
+constexpr int F_CAP = 6 * 1024;    // field box floats (6 components)
+constexpr int J_CAP = 3 * 1024;    // current box floats (3 components)
+constexpr int SMEM_2D = F_CAP + J_CAP;
+
+// 4-byte asynchronous global -> shared copy (the next chunk's particle data)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // floor(i / d) for 0 <= i < 2^22 from r = 1/d rounded to nearest: (i + 1/2) r is within
 // (i + 1/2) 2^-23 / d of (i + 1/2) / d, which lies at least 1/(2d) from an integer.
@@ -898,6 +907,8 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
 // every contribution).
 constexpr int F_CAP3 = 8192;       // 3D field box floats (6 components)
 constexpr int J_CAP3 = 9216;       // 3D current box ints (3 components)
+constexpr int PF3 = 7;             // prefetched words per particle (cell, 3 offsets, 3 momenta)
+constexpr int SMEM_3D = F_CAP3 + J_CAP3 + 2 * PF3 * FUSED_T;
 
 // .x = sum Wza Wxa Wya Fa, .y = sum Wzb Wxb Wyb Fb over K^3 nodes of [y][x][z] boxes (row fzl,
 // fxl rows per plane); (z, x, y) are the stencil origins in the box.
@@ -937,28 +948,48 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
     const int N = (int)g.ncell;
     const bool fvec = (g.nz & 3) == 0 && aligned16(E) && aligned16(B);
     const bool jvec = (g.nz & 3) == 0 && aligned16(J);
-    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T) {
+    float* const pfb = sJ + J_CAP3;                   // [2][PF3][FUSED_T]
+    auto prefetch = [&](long long b, int buf) {
+        const long long q = b + threadIdx.x;
+        if (q < n) {
+            float* d = pfb + buf * PF3 * FUSED_T + threadIdx.x;
+            cp_async4(d, sp.cell + q);
+            cp_async4(d + FUSED_T, sp.off + q);
+            cp_async4(d + 2 * FUSED_T, sp.off + cap + q);
+            cp_async4(d + 3 * FUSED_T, sp.off + 2 * cap + q);
+            cp_async4(d + 4 * FUSED_T, sp.u + q);
+            cp_async4(d + 5 * FUSED_T, sp.u + cap + q);
+            cp_async4(d + 6 * FUSED_T, sp.u + 2 * cap + q);
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    prefetch(chunk0 * FUSED_T, 0);
+    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T, buf ^= 1) {
         if (threadIdx.x < 7) box[threadIdx.x] = threadIdx.x == 6 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        prefetch(base + stride * FUSED_T, buf ^ 1);
+        cp_async_wait_prev();
         __syncthreads();
         const long long p = base + threadIdx.x;
+        const float* mine = pfb + buf * PF3 * FUSED_T + threadIdx.x;
         // ---- load and decode ----
         bool ok = false;
         Pos p0;
         float u[3] = {0.f, 0.f, 0.f};
         if (p < n) {
-            int cell = sp.cell[p];
+            int cell = __float_as_int(mine[0]);
             if (cell >= 0) {
                 int izg;
                 decode(g, cell, izg, p0.ix, p0.iy);
                 p0.iz = izg - 1 - shift;
                 if (p0.iz >= 0 && p0.iz < g.nz) {
                     ok = true;
-                    p0.oz = sp.off[p];
-                    p0.ox = sp.off[cap + p];
-                    p0.oy = sp.off[2 * cap + p];
-                    u[0] = sp.u[p];
-                    u[1] = sp.u[cap + p];
-                    u[2] = sp.u[2 * cap + p];
+                    p0.oz = mine[FUSED_T];
+                    p0.ox = mine[2 * FUSED_T];
+                    p0.oy = mine[3 * FUSED_T];
+                    u[0] = mine[4 * FUSED_T];
+                    u[1] = mine[5 * FUSED_T];
+                    u[2] = mine[6 * FUSED_T];
                 } else {
                     sp.cell[p] = -1;
                 }
@@ -1506,7 +1537,7 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
         constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
         if (mode == MODE_FUSED && ND == 2) {
             auto k = push_deposit_2d_kernel<SH>;
-            const size_t smem = (F_CAP + J_CAP) * sizeof(float);
+            const size_t smem = SMEM_2D * sizeof(float);
             static bool configured = false;
             if (!configured) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1516,7 +1547,7 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
             k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift);
         } else if (mode == MODE_FUSED) {
             auto k = push_deposit_3d_kernel<SH>;
-            const size_t smem = (F_CAP3 + J_CAP3) * sizeof(float);
+            const size_t smem = SMEM_3D * sizeof(float);
             static bool configured = false;
             if (!configured) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1540,7 +1571,7 @@ cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int sha
         constexpr int ND = decltype(nd)::value, SH = decltype(sh)::value;
         if (ND == 2) {
             auto k = push_deposit_2d_batch_kernel<SH>;
-            const size_t smem = (F_CAP + J_CAP) * sizeof(float);
+            const size_t smem = SMEM_2D * sizeof(float);
             static bool configured = false;
             if (!configured) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1551,7 +1582,7 @@ cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int sha
             return cudaGetLastError();
         }
         auto k = push_deposit_3d_batch_kernel<SH>;
-        const size_t smem = (F_CAP3 + J_CAP3) * sizeof(float);
+        const size_t smem = SMEM_3D * sizeof(float);
         static bool configured = false;
         if (!configured) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
