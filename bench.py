@@ -165,7 +165,7 @@ def emit(obj):
 # SHA-1 of the source file the capture was built from
 TRAFFIC_SOURCES = {
     ("particles", 2): ("profiles/push_deposit_2d_beam_plasma_2d.md", "paper_1910_13529_gb300/csrc/particle_kernels.cu"),
-    ("particles", 3): ("profiles/push_deposit_3d_beam_plasma_3d.md", "paper_1910_13529_gb300/csrc/particle_kernels.cu"),
+    ("particles", 3): ("profiles/push_deposit_3d_beam_plasma_3d_small.md", "paper_1910_13529_gb300/csrc/particle_kernels.cu"),
 }
 
 
