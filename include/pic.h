@@ -241,7 +241,9 @@ pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const floa
  * pic_get_tuning: chosen variant, per-variant time in ms (0: not timed; ms needs
  * PIC_MAX_TILE_VARIANTS entries) and the number of variants.  2D (z x x): 0 = 128x8,
  * 1 = 256x4, 2 = 64x16, 3 = 256x8 with one cell per thread and stage, 4 = 128x8, 5 = 256x4,
- * 6 = 128x4, 7 = 256x8 register-blocked (four z cells per thread, 128-bit shared loads);
+ * 6 = 128x4, 7 = 256x8 register-blocked (four z cells per thread, 128-bit shared loads),
+ * 8..11 register-blocked z segments of 448, 384, 960, 192 cells that march along x with the
+ * next rows prefetched;
  * 3D (z x x x y): 0 = 64x4x4, 1 = 128x4x2, 2 = 32x8x4, 3..5 the same shapes register-
  * blocked, 6..9 register-blocked columns that march along y (z x x = 128x4 with 256 or 128
  * threads, 128x8, 64x8).  Without pic_autotune a handle uses 0 for Yee and the register-

@@ -729,6 +729,249 @@ __device__ __forceinline__ void march_bnew_store(const FieldP& p, const float* e
     }
 }
 
+// ---- 2D x-marching rows -------------------------------------------------------------------
+// A CTA owns z in [z0, z0 + TZ) and walks x over [xa, xa + xc): every row of B^{n+1/2} and
+// E^{n+1} is computed once (no x halo), register-blocked along z as above.  The rows a step
+// needs next are copied by cp.async one step ahead into a ring of 4 E, 3 B and 2 J rows:
+// for output row k the step computes B^{n+1/2}(k+1) from E^n(k+1), E^n(k+2); E^{n+1}(k+1) from
+// B^{n+1/2}(k+1), B^{n+1/2}(k), J(k+1); B^{n+1}(k) from E^{n+1}(k), E^{n+1}(k+1), B^{n+1/2}(k),
+// while E^n(k+3), B^n(k+2), J(k+2) land.
+template <int MAXM, int TZ>
+struct March2T {
+    static constexpr int MP = (MAXM + 3) & ~3;
+    static constexpr int H2 = MP, H1 = 2 * MP, H0 = 3 * MP;
+    static constexpr int WE = TZ + 2 * H0, WB = TZ + 2 * H1, WJ = TZ + 2 * H2;
+    static constexpr int SE = 3 * WE, SB = 3 * WB, SJ = 3 * WJ;           // one row, 3 components
+    static constexpr size_t smem_bytes = sizeof(float) * (4 * SE + 3 * SB + 2 * SJ);
+    static_assert(TZ % 4 == 0, "the z tile holds whole groups of four cells");
+};
+
+// B^{n+1/2} in place over the B^n row b from the E^n rows e (x) and e1 (x + 1).
+template <int MAXM, int TZ>
+__device__ __forceinline__ void march2_bhalf(const FieldP& p, float* b, const float* e, const float* e1, int z0) {
+    using T = March2T<MAXM, TZ>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, NG = WB / 4;
+    const GridP& g = p.g;
+    const float hz = 0.5f * g.dt / g.dz, hx = 0.5f * g.dt / g.dx;
+    for (int gi = threadIdx.x; gi < NG; gi += blockDim.x) {
+        const int z = 4 * gi - T::H1, gz = z0 + z;
+        if (gz + 3 < 0 || gz >= g.nz) continue;                     // B^n = B^{n+1/2} = 0 there
+        const int eo = z + T::H0;
+        float d2[4], d3[4], E2[4], E3[4], E1[4], E1x[4], E3x[4];
+        window_dz<MAXM, MP, true>(p.st, e + WE + eo - MP, d2, E2);
+        window_dz<MAXM, MP, true>(p.st, e + 2 * WE + eo - MP, d3, E3);
+        lds4(E1, e + eo);
+        lds4(E1x, e1 + eo);
+        lds4(E3x, e1 + 2 * WE + eo);
+        const int bo = 4 * gi;
+        float b0[4], b1[4], b2[4];
+        lds4(b0, b + bo);
+        lds4(b1, b + WB + bo);
+        lds4(b2, b + 2 * WB + bo);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const bool in = gz + j >= 0 && gz + j < g.nz;
+            b0[j] = in ? b0[j] - hx * (E3x[j] - E3[j]) : 0.f;
+            b1[j] = in ? b1[j] + hz * d3[j] : 0.f;
+            b2[j] = in ? b2[j] - (hz * d2[j] - hx * (E1x[j] - E1[j])) : 0.f;
+        }
+        sts4(b + bo, b0);
+        sts4(b + WB + bo, b1);
+        sts4(b + 2 * WB + bo, b2);
+    }
+}
+
+// E^{n+1} in place over the E^n row e from the B^{n+1/2} rows b (x), bm (x - 1) and the J row j.
+template <int MAXM, int TZ>
+__device__ __forceinline__ void march2_enew(const FieldP& p, float* e, const float* b, const float* bm, const float* j,
+                                            int z0) {
+    using T = March2T<MAXM, TZ>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, WJ = T::WJ, NG = WJ / 4;
+    const GridP& g = p.g;
+    const float dt = g.dt, fz = dt / g.dz, fx = dt / g.dx;
+    for (int gi = threadIdx.x; gi < NG; gi += blockDim.x) {
+        const int z = 4 * gi - T::H2, gz = z0 + z;
+        if (gz + 3 < 0 || gz >= g.nz) continue;                     // E^n = E^{n+1} = 0 there
+        const int eo = z + T::H0, bo = z + T::H1;
+        float d2[4], d3[4], B2[4], B3[4], B1[4], B1x[4], B3x[4];
+        window_dz<MAXM, MP, false>(p.st, b + WB + bo - MP, d2, B2);
+        window_dz<MAXM, MP, false>(p.st, b + 2 * WB + bo - MP, d3, B3);
+        lds4(B1, b + bo);
+        lds4(B1x, bm + bo);
+        lds4(B3x, bm + 2 * WB + bo);
+        const int jo = 4 * gi;
+        float e0[4], e1[4], e2[4], j0[4], j1[4], j2[4];
+        lds4(e0, e + eo);
+        lds4(e1, e + WE + eo);
+        lds4(e2, e + 2 * WE + eo);
+        lds4(j0, j + jo);
+        lds4(j1, j + WJ + jo);
+        lds4(j2, j + 2 * WJ + jo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool in = gz + q >= 0 && gz + q < g.nz;
+            e0[q] = in ? e0[q] + fx * (B3[q] - B3x[q]) - dt * j0[q] : 0.f;
+            e1[q] = in ? e1[q] - fz * d3[q] - dt * j1[q] : 0.f;
+            e2[q] = in ? e2[q] + (fz * d2[q] - fx * (B1[q] - B1x[q])) - dt * j2[q] : 0.f;
+        }
+        sts4(e + eo, e0);
+        sts4(e + WE + eo, e1);
+        sts4(e + 2 * WE + eo, e2);
+    }
+}
+
+// B^{n+1} of row gx from the E^{n+1} rows e (x), e1 (x + 1) and the B^{n+1/2} row b; stores
+// E^{n+1}(x), B^{n+1}(x) (one cell towards -z if the window moves).
+template <int MAXM, int TZ>
+__device__ __forceinline__ void march2_bnew_store(const FieldP& p, const float* e, const float* e1, const float* b,
+                                                  int z0, int gx, bool vec) {
+    using T = March2T<MAXM, TZ>;
+    constexpr int MP = T::MP, WE = T::WE, WB = T::WB, NG = TZ / 4;
+    const GridP& g = p.g;
+    const long long N = g.ncell;
+    const float hz = 0.5f * g.dt / g.dz, hx = 0.5f * g.dt / g.dx;
+    const long long row = (long long)gx * g.nz;
+    for (int gi = threadIdx.x; gi < NG; gi += blockDim.x) {
+        const int z = 4 * gi, gz = z0 + z;
+        if (gz >= g.nz) continue;
+        const int eo = z + T::H0, bo = z + T::H1;
+        float d2[4], d3[4], E2[4], E3[4], E1[4], E1x[4], E3x[4];
+        window_dz<MAXM, MP, true>(p.st, e + WE + eo - MP, d2, E2);
+        window_dz<MAXM, MP, true>(p.st, e + 2 * WE + eo - MP, d3, E3);
+        lds4(E1, e + eo);
+        lds4(E1x, e1 + eo);
+        lds4(E3x, e1 + 2 * WE + eo);
+        float b0[4], b1[4], b2[4];
+        lds4(b0, b + bo);
+        lds4(b1, b + WB + bo);
+        lds4(b2, b + 2 * WB + bo);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            b0[q] -= hx * (E3x[q] - E3[q]);
+            b1[q] += hz * d3[q];
+            b2[q] -= hz * d2[q] - hx * (E1x[q] - E1[q]);
+        }
+        if (vec && !p.shift) {
+            const long long o = row + gz;
+            *reinterpret_cast<float4*>(p.Eout + o) = make_float4(E1[0], E1[1], E1[2], E1[3]);
+            *reinterpret_cast<float4*>(p.Eout + N + o) = make_float4(E2[0], E2[1], E2[2], E2[3]);
+            *reinterpret_cast<float4*>(p.Eout + 2 * N + o) = make_float4(E3[0], E3[1], E3[2], E3[3]);
+            *reinterpret_cast<float4*>(p.Bout + o) = make_float4(b0[0], b0[1], b0[2], b0[3]);
+            *reinterpret_cast<float4*>(p.Bout + N + o) = make_float4(b1[0], b1[1], b1[2], b1[3]);
+            *reinterpret_cast<float4*>(p.Bout + 2 * N + o) = make_float4(b2[0], b2[1], b2[2], b2[3]);
+            continue;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gzq = gz + q;
+            if (gzq >= g.nz) break;
+            const int oz = gzq - p.shift;
+            if (oz >= 0) {
+                const long long o = row + oz;
+                p.Eout[o] = E1[q];
+                p.Eout[N + o] = E2[q];
+                p.Eout[2 * N + o] = E3[q];
+                p.Bout[o] = b0[q];
+                p.Bout[N + o] = b1[q];
+                p.Bout[2 * N + o] = b2[q];
+            }
+            if (p.shift && gzq == g.nz - 1) {
+                const long long o = row + gzq;
+                p.Eout[o] = 0.f;
+                p.Eout[N + o] = 0.f;
+                p.Eout[2 * N + o] = 0.f;
+                p.Bout[o] = 0.f;
+                p.Bout[N + o] = 0.f;
+                p.Bout[2 * N + o] = 0.f;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev_group() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <int MAXM, int TZ, int NT>
+__global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int xc) {
+    using T = March2T<MAXM, TZ>;
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const GridP& g = p.g;
+    const long long N = g.ncell;
+    const bool vec = p.vec4 != 0;
+    const int z0 = blockIdx.x * TZ;
+    const int xa = blockIdx.y * xc, xb = min(xa + xc, g.nx);
+    auto Eslot = [&](int i) { return sm + i * T::SE; };
+    auto Bslot = [&](int i) { return sm + 4 * T::SE + i * T::SB; };
+    auto Jslot = [&](int i) { return sm + 4 * T::SE + 3 * T::SB + i * T::SJ; };
+    auto stageE = [&](int i, int x) {
+        stage_plane(Eslot(i), T::WE, p.Ein, p.Ein + N, p.Ein + 2 * N, 1, T::WE, z0 - T::H0, wrapi(x, g.nx), 0, 0, g,
+                    vec);
+    };
+    auto stageB = [&](int i, int x) {
+        stage_plane(Bslot(i), T::WB, p.Bin, p.Bin + N, p.Bin + 2 * N, 1, T::WB, z0 - T::H1, wrapi(x, g.nx), 0, 0, g,
+                    vec);
+    };
+    auto stageJ = [&](int i, int x) {
+        stage_plane(Jslot(i), T::WJ, p.J1, p.J2, p.J3, 1, T::WJ, z0 - T::H2, wrapi(x, g.nx), 0, 0, g, vec);
+    };
+    auto landed_all = [&]() {
+        if (vec) cp_async_wait_all();
+        __syncthreads();
+    };
+    // prologue: B^{n+1/2}(xa-1), B^{n+1/2}(xa), E^{n+1}(xa), and the first prefetch
+    stageE(0, xa - 1);
+    stageE(1, xa);
+    stageB(0, xa - 1);
+    landed_all();
+    march2_bhalf<MAXM, TZ>(p, Bslot(0), Eslot(0), Eslot(1), z0);
+    stageE(2, xa + 1);
+    stageB(1, xa);
+    stageJ(0, xa);
+    landed_all();
+    march2_bhalf<MAXM, TZ>(p, Bslot(1), Eslot(1), Eslot(2), z0);
+    __syncthreads();
+    march2_enew<MAXM, TZ>(p, Eslot(1), Bslot(1), Bslot(0), Jslot(0), z0);
+    __syncthreads();
+    // E: ec = E^{n+1}(k), en = E^n(k+1), ef = E^n(k+2) (in flight), eg = free
+    // B: bc = B^{n+1/2}(k), bf = B^n(k+1) (in flight), bg = free;  J: jf = J(k+1) (in flight), jg = free
+    int ec = 1, en = 2, ef = 3, eg = 0, bc = 1, bf = 2, bg = 0, jf = 1, jg = 0;
+    stageE(ef, xa + 2);
+    stageB(bf, xa + 1);
+    stageJ(jf, xa + 1);
+    if (vec) cp_async_commit_group();
+    for (int k = xa; k < xb; ++k) {
+        // the next step's rows, while this step computes
+        stageE(eg, k + 3);
+        stageB(bg, k + 2);
+        stageJ(jg, k + 2);
+        if (vec) {
+            cp_async_commit_group();
+            cp_async_wait_prev_group();             // this step's rows (committed one step earlier)
+        }
+        __syncthreads();
+        march2_bhalf<MAXM, TZ>(p, Bslot(bf), Eslot(en), Eslot(ef), z0);
+        __syncthreads();
+        march2_enew<MAXM, TZ>(p, Eslot(en), Bslot(bf), Bslot(bc), Jslot(jf), z0);
+        __syncthreads();
+        march2_bnew_store<MAXM, TZ>(p, Eslot(ec), Eslot(en), Bslot(bc), z0, k, vec);
+        __syncthreads();
+        int t = ec;
+        ec = en;
+        en = ef;
+        ef = eg;
+        eg = t;
+        t = bc;
+        bc = bf;
+        bf = bg;
+        bg = t;
+        t = jf;
+        jf = jg;
+        jg = t;
+    }
+    if (vec) cp_async_wait_all();                   // no copy may outlive the CTA's shared memory
+}
+
 template <int MAXM, int TZ, int TX, int NT>
 __global__ void __launch_bounds__(NT) field_advance_march_kernel(FieldP p, int yc) {
     using T = MarchT<MAXM, TZ, TX>;
@@ -887,6 +1130,33 @@ cudaError_t launch_fa_march(const FieldP& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int MAXM, int TZ, int NT>
+cudaError_t launch_fa_march2(const FieldP& p, cudaStream_t s) {
+    using T = March2T<MAXM, TZ>;
+    auto k = field_advance_march2_kernel<MAXM, TZ, NT>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // x chunks: one wave of CTAs over the SMs, each chunk at least 16 rows (the prologue of a
+    // chunk recomputes two rows)
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int cols = (p.g.nz + TZ - 1) / TZ;
+    int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2048 / NT ? 2048 / NT : per_sm);
+    int chunks = (int)(((long long)nsm * per_sm + cols - 1) / cols);
+    chunks = chunks < 1 ? 1 : chunks;
+    int xc = (p.g.nx + chunks - 1) / chunks;
+    xc = xc < 16 ? 16 : xc;
+    dim3 grid(cols, (p.g.nx + xc - 1) / xc, 1);
+    k<<<grid, NT, T::smem_bytes, s>>>(p, xc);
+    return cudaGetLastError();
+}
+
 // In-place Sec. 3 correction J1[i] <- sum_{|m| <= hlen} h[m] J1[i - m] along z (J1 = 0 outside
 // 0 <= i < nz).  One CTA holds a whole z row in shared memory, so no other CTA reads the values
 // it overwrites.
@@ -987,12 +1257,14 @@ cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_row
 // Tile variants the autotuner chooses from.  2D: (TZ, TX); 3D: (TZ, TX, TY); rb = register-
 // blocked tile (four z cells per thread).
 //   2D: 0 = 128 x 8, 1 = 256 x 4, 2 = 64 x 16, 3 = 256 x 8,
-//       4 = rb 128 x 8, 5 = rb 256 x 4, 6 = rb 128 x 4, 7 = rb 256 x 8
+//       4 = rb 128 x 8, 5 = rb 256 x 4, 6 = rb 128 x 4, 7 = rb 256 x 8,
+//       8 = x-march z 448 (128 threads), 9 = x-march z 384 (128 threads),
+//       10 = x-march z 960 (256 threads), 11 = x-march z 192 (64 threads)
 //   3D: 0 = 64 x 4 x 4, 1 = 128 x 4 x 2, 2 = 32 x 8 x 4,
 //       3 = rb 64 x 4 x 4, 4 = rb 128 x 4 x 2, 5 = rb 32 x 8 x 4,
 //       6 = y-march 128 x 4 (256 threads), 7 = y-march 128 x 4 (128 threads),
 //       8 = y-march 128 x 8 (256 threads), 9 = y-march 64 x 8 (256 threads)
-int field_variants(int ndim) { return ndim == 2 ? 8 : 10; }
+int field_variants(int ndim) { return ndim == 2 ? 12 : 10; }
 
 // Variant used before (or without) pic_autotune: the register-blocked tile for the customised
 // stencils, the scalar tile for Yee.
@@ -1013,6 +1285,10 @@ cudaError_t launch_fa_variant(const FieldP& p, int v, cudaStream_t s) {
             case 5: return launch_fa_rb<2, MAXM, 256, 4, 1>(p, s);
             case 6: return launch_fa_rb<2, MAXM, 128, 4, 1>(p, s);
             case 7: return launch_fa_rb<2, MAXM, 256, 8, 1>(p, s);
+            case 8: return launch_fa_march2<MAXM, 448, 128>(p, s);
+            case 9: return launch_fa_march2<MAXM, 384, 128>(p, s);
+            case 10: return launch_fa_march2<MAXM, 960, 256>(p, s);
+            case 11: return launch_fa_march2<MAXM, 192, 64>(p, s);
             default: return launch_fa<2, MAXM, 128, 8, 1>(p, s);
         }
     }
