@@ -131,8 +131,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_baseline(grid, sps, frac=0.1, seed=0):
-    """FP64 oracle on the host: the full grid and a random fraction of the particles, one step."""
+def oracle_baseline(grid, sps, frac=0.25, seed=0, steps=2):
+    """FP64 oracle on the host: the full grid and a random fraction of the particles, `steps`
+    steps; returns (particle pushes per second, seconds, particles)."""
     from oracle import core as oc
     from oracle import fit
     from paper_1910_13529_gb300 import workloads as wl
@@ -152,9 +153,10 @@ def oracle_baseline(grid, sps, frac=0.1, seed=0):
         n += int(sel.sum())
     sim = oc.Sim(g, species, h=h, moving_window=True)
     t0 = time.perf_counter()
-    sim.step()
+    for _ in range(steps):
+        sim.step()
     dt = time.perf_counter() - t0
-    return n / dt, dt, n
+    return n * steps / dt, dt, n
 
 
 def emit(obj):
@@ -216,7 +218,7 @@ def run_reference(args, rank, world):
     vals, times = [], []
     # the oracle has nothing to warm up; at most three timed samples keep the run within minutes
     for k in range(max(1, min(args.steps, 3))):
-        v, dt, n = oracle_baseline(grid, sps, frac=0.05, seed=k)
+        v, dt, n = oracle_baseline(grid, sps, frac=0.05, seed=k, steps=1)
         vals.append(v)
         times.append(dt)
     value = float(np.median(vals))
@@ -264,17 +266,22 @@ def run_ours(args, rank, world, local_rank):
     d0 = sim.diag()
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    pic_timing(sim.h, 1)
     with ClockSampler(local_rank) as clk:
         ev0.record()
         sim.step(args.steps)
         ev1.record()
         torch.cuda.synchronize(dev)
-    kms, klaunch = pic_timing_read(sim.h, stream)
-    pic_timing(sim.h, 0)
     barrier()
     ms = ev0.elapsed_time(ev1)
     d1 = sim.diag()
+    # per-kernel-class times (CUDA events around every launch, on the launch stream) from a second
+    # timed pass of the same length, so that the instrumentation stays out of the headline number
+    pic_timing(sim.h, 1)
+    sim.step(args.steps)
+    kms, klaunch = pic_timing_read(sim.h, stream)
+    pic_timing(sim.h, 0)
+    d2 = sim.diag()
+    barrier()
     pushes_per_step = 0.5 * (d0["count"] + d1["count"])
     ms_max, total_pushes, value = aggregate(ms, pushes_per_step, args.steps, world, dev)
     cells = grid["nz"] * grid["nx"] * grid.get("ny", 1)
@@ -284,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kms, key=kms.get)
     peak, peak_kind = measured_peak()
     if dom == "particles":
-        algo = bpp * pushes_per_step * args.steps
+        algo = bpp * 0.5 * (d1["count"] + d2["count"]) * args.steps
     else:
         algo = BYTES_PER_CELL_UPDATE * cells * args.steps
     achieved = algo / (kms[dom] / 1e3) / 1e9
@@ -337,9 +344,9 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 2:
-        v, dt, n = oracle_baseline(grid, sps, frac=0.05)
+        v, dt, n = oracle_baseline(grid, sps, frac=0.25, steps=2)
         cpu = {"value": v, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle step, full {grid['nz']}x{grid['nx']} grid, 5% random particle "
+               "sample": f"two FP64 oracle steps, full {grid['nz']}x{grid['nx']} grid, 25% random particle "
                          f"sample ({n} particles), {dt:.1f} s single-threaded"}
     if rank == 0:
         launches = int(sum(klaunch.values()))

@@ -813,10 +813,11 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
                 Ax[k] = g3 * tx;
                 Bx[k] = g3 * (0.5f * S0x[k] + (1.f / 3.f) * DSx[k]);
             }
-            // Lanes sharing a window hit the same nodes.  With at most 4 lanes per window anywhere
-            // in the warp every live lane adds its own values (at most 4-way address conflicts);
-            // otherwise (dense beams) runs of consecutive lanes are summed first and one lane per
-            // run adds the total.  Empty slots have unique keys.
+            // Lanes sharing a window hit the same nodes.  With at most 8 lanes per window anywhere
+            // in the warp every live lane adds its own values (at most 8-way address conflicts,
+            // serialised by the shared-memory pipe); otherwise (dense beams) runs of consecutive
+            // lanes are summed first and one lane per run adds the total.  Empty slots have unique
+            // keys.
             const unsigned long long key = ok ? (((unsigned long long)(bz + 4) << 32) | (unsigned)(bx + 4))
                                               : (0xFFFFFFFF00000000ull | (unsigned)threadIdx.x);
             const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
@@ -840,7 +841,7 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
                         put(2 * jvol + o, fmaf(S0z[a], Ax[b], fmaf(DSz[a], Bx[b], MAGIC)));
                     }
             };
-            if (gmax <= 4) {
+            if (gmax <= 8) {
                 if (ok) terms([&](int o, float biased) { atomicAdd(s0 + o, __float_as_int(biased) - 0x4B400000); });
             } else {
                 const SegReduce seg = make_segments(key);

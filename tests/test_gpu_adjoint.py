@@ -96,7 +96,7 @@ def test_autograd_wrapper_and_descent_step():
     C1 = C4 - step * gp
     assert abs(w @ C1 - 1.0) < 1e-12
     assert fit.cfl_dt(grid["dz"], [grid["dx"]], C1) > grid["dt"]
-    assert problem.loss(C1) < float(L)
+    assert problem.loss(C1) < float(L.detach())
 
 
 def _golden():
