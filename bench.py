@@ -344,9 +344,9 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 2:
-        v, dt, n = oracle_baseline(grid, sps, frac=0.25, steps=2)
+        v, dt, n = oracle_baseline(grid, sps, frac=0.5, steps=2)
         cpu = {"value": v, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
-               "sample": f"two FP64 oracle steps, full {grid['nz']}x{grid['nx']} grid, 25% random particle "
+               "sample": f"two FP64 oracle steps, full {grid['nz']}x{grid['nx']} grid, 50% random particle "
                          f"sample ({n} particles), {dt:.1f} s single-threaded"}
     if rank == 0:
         launches = int(sum(klaunch.values()))

@@ -880,7 +880,10 @@ pic_status batch_build(pic_batch_t* b) {
             CorrInst c;
             c.g = h->g;
             c.hlen = h->hlen;
-            for (int k = 0; k < 2 * PIC_MAX_HLEN + 1; ++k) c.h[k] = k < 2 * h->hlen + 1 ? h->hf[k] : 0.f;
+            for (int k = 0; k < 2 * PIC_MAX_HLEN + 1; ++k) {     // centred on PIC_MAX_HLEN
+                const int m = k - PIC_MAX_HLEN;
+                c.h[k] = (m >= -h->hlen && m <= h->hlen) ? h->hf[m + h->hlen] : 0.f;
+            }
             c.J1 = h->J;
             corr.push_back(c);
             long long rows = (long long)h->g.nx * h->g.ny;
