@@ -507,6 +507,7 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_p() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 // floor(i / d) for 0 <= i < 2^22 from r = 1/d rounded to nearest: (i + 1/2) r is within
@@ -966,11 +967,19 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
     };
     int buf = 0;
     prefetch(chunk0 * FUSED_T, 0);
-    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T, buf ^= 1) {
-        if (threadIdx.x < 7) box[threadIdx.x] = threadIdx.x == 6 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+    // box[0..6] and box[7..13] serve alternate chunks (see push_deposit_2d_chunks): no barrier at
+    // the top of the loop or after the flush
+    if (threadIdx.x < 14) {
+        const int q = threadIdx.x % 7;
+        box[threadIdx.x] = q == 6 ? 0 : (q & 1) ? INT_MIN : INT_MAX;
+    }
+    __syncthreads();
+    int cur = 0;
+    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T, buf ^= 1, cur ^= 7) {
+        int* const bc = box + cur;
+        if (threadIdx.x < 7) box[(cur ^ 7) + threadIdx.x] = threadIdx.x == 6 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
         prefetch(base + stride * FUSED_T, buf ^ 1);
-        cp_async_wait_prev();
-        __syncthreads();
+        cp_async_wait_prev();                      // this thread's words of this chunk
         const long long p = base + threadIdx.x;
         const float* mine = pfb + buf * PF3 * FUSED_T + threadIdx.x;
         // ---- load and decode ----
@@ -1007,26 +1016,26 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
             byn = p0.iy + Shape<SHAPE>::w(p0.oy, Wyn);
             byh = half_weights<SHAPE>(p0.iy, p0.oy, Wyh);
         }
-        box_reduce(box, ok ? min(bzn, bzh) : INT_MAX, ok ? max(bzn, bzh) + K - 1 : INT_MIN,
+        box_reduce(bc, ok ? min(bzn, bzh) : INT_MAX, ok ? max(bzn, bzh) + K - 1 : INT_MIN,
                    ok ? min(bxn, bxh) : INT_MAX, ok ? max(bxn, bxh) + K - 1 : INT_MIN);
         {
             const int c = __reduce_min_sync(0xffffffffu, ok ? min(byn, byh) : INT_MAX);
             const int d = __reduce_max_sync(0xffffffffu, ok ? max(byn, byh) + K - 1 : INT_MIN);
             if ((threadIdx.x & 31) == 0 && c != INT_MAX) {
-                atomicMin(box + 4, c);
-                atomicMax(box + 5, d);
+                atomicMin(bc + 4, c);
+                atomicMax(bc + 5, d);
             }
         }
         __syncthreads();
-        const bool any = box[0] != INT_MAX;
-        const int fz0 = any ? (box[0] & ~3) : 0, fx0 = box[2], fy0 = box[4];
-        const int fzl = any ? ((box[1] + 1 - fz0 + 3) & ~3) : 0;
-        const int fxl = any ? box[3] - box[2] + 1 : 0, fyl = any ? box[5] - box[4] + 1 : 0;
+        const bool any = bc[0] != INT_MAX;
+        const int fz0 = any ? (bc[0] & ~3) : 0, fx0 = bc[2], fy0 = bc[4];
+        const int fzl = any ? ((bc[1] + 1 - fz0 + 3) & ~3) : 0;
+        const int fxl = any ? bc[3] - bc[2] + 1 : 0, fyl = any ? bc[5] - bc[4] + 1 : 0;
         const int fvol = fzl * fxl * fyl;
         const bool ftile = any && 6 * fvol <= F_CAP3 && fxl <= g.nx + 2 * K && fyl <= g.ny + 2 * K;
-        const int jz0 = any ? ((box[0] - 1) & ~3) : 0, jx0 = box[2] - 1, jy0 = box[4] - 1;
-        const int jzl = any ? ((box[1] + 3 - jz0 + 3) & ~3) : 0;
-        const int jxl = any ? box[3] - box[2] + 4 : 0, jyl = any ? box[5] - box[4] + 4 : 0;
+        const int jz0 = any ? ((bc[0] - 1) & ~3) : 0, jx0 = bc[2] - 1, jy0 = bc[4] - 1;
+        const int jzl = any ? ((bc[1] + 3 - jz0 + 3) & ~3) : 0;
+        const int jxl = any ? bc[3] - bc[2] + 4 : 0, jyl = any ? bc[5] - bc[4] + 4 : 0;
         const int jvol = jzl * jxl * jyl;
         const bool jtile = any && 3 * jvol <= J_CAP3 && jxl <= g.nx + 2 * KW && jyl <= g.ny + 2 * KW;
         if (ftile) {
@@ -1127,10 +1136,10 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
         // fixed-point scale of the chunk (see push_deposit_2d_chunks): s = 2^(22-e), max mb < 2^e
         if (jtile) {
             const unsigned wm = __reduce_max_sync(0xffffffffu, ok ? __float_as_uint(mb) : 0u);
-            if ((threadIdx.x & 31) == 0 && wm) atomicMax(reinterpret_cast<unsigned*>(box + 6), wm);
+            if ((threadIdx.x & 31) == 0 && wm) atomicMax(reinterpret_cast<unsigned*>(bc + 6), wm);
         }
         __syncthreads();
-        const int mbits = box[6];
+        const int mbits = bc[6];
         const int sexp = min(275 - (mbits >> 23), 253);
         const float fs = __int_as_float(sexp << 23), inv_s = __int_as_float((254 - sexp) << 23);
         int* const iJ = reinterpret_cast<int*>(sJ);
@@ -1207,8 +1216,8 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
                 }
             }
         }
-        __syncthreads();
     }
+    cp_async_wait_all_p();                         // the last (empty) prefetch group
 }
 
 template <int SHAPE>
@@ -1217,7 +1226,7 @@ __global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_kernel(GridP g, Sp
                                                                      int shift) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    __shared__ int box[7];
+    __shared__ int box[14];
     push_deposit_3d_chunks<SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + F_CAP3, box);
 }
 
@@ -1225,7 +1234,7 @@ template <int SHAPE>
 __global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_batch_kernel(const PartInst* __restrict__ inst, int parity) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
-    __shared__ int box[7];
+    __shared__ int box[14];
     const PartInst& q = inst[blockIdx.y];
     const GridP g = prep_device(q.g);
     push_deposit_3d_chunks<SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem,
@@ -1349,12 +1358,17 @@ __device__ __forceinline__ int sort_key(const GridP& g, int cell) {
     return ((iy * ntx + (ix >> 3)) * ntz + (izg >> 3)) * 64 + ((ix & 7) << 3) + (izg & 7);
 }
 
+// Cell-sorted particles come in runs of equal keys: the lanes of a warp with one key add their
+// count with one atomic (the loop trip count is uniform across a warp).
 __global__ void hist_kernel(GridP g, SpeciesP sp, int32_t* hist) {
     const long long n = *sp.count;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+    const int lane = threadIdx.x & 31;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p - lane < n;
          p += (long long)gridDim.x * blockDim.x) {
-        int c = sp.cell[p];
-        if (c >= 0) atomicAdd(hist + sort_key(g, c), 1);
+        const int c = p < n ? sp.cell[p] : -1;
+        const int key = c >= 0 ? sort_key(g, c) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(hist + key, __popc(grp));
     }
 }
 
@@ -1437,11 +1451,19 @@ __global__ void scatter_kernel(GridP g, SpeciesP sp, int32_t* cursor, int32_t* c
                                int32_t* id2) {
     const long long n = *sp.count;
     const long long cap = sp.cap;
-    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+    const int lane = threadIdx.x & 31;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p - lane < n;
          p += (long long)gridDim.x * blockDim.x) {
-        int c = sp.cell[p];
-        if (c < 0) continue;
-        long long d = atomicAdd(cursor + sort_key(g, c), 1);
+        // one cursor atomic per key and warp; lanes keep their order within the key
+        const int c = p < n ? sp.cell[p] : -1;
+        const int key = c >= 0 ? sort_key(g, c) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(grp) - 1;
+        int first = 0;
+        if (key >= 0 && lane == leader) first = atomicAdd(cursor + key, __popc(grp));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (key < 0) continue;
+        const long long d = (long long)first + __popc(grp & ((1u << lane) - 1u));
         cell2[d] = c;
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) off2[k * cap + d] = sp.off[k * cap + p];
