@@ -246,7 +246,8 @@ pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const floa
  * next rows prefetched;
  * 3D (z x x x y): 0 = 64x4x4, 1 = 128x4x2, 2 = 32x8x4, 3..5 the same shapes register-
  * blocked, 6..9 register-blocked columns that march along y (z x x = 128x4 with 256 or 128
- * threads, 128x8, 64x8).  Without pic_autotune a handle uses 0 for Yee and the register-
+ * threads, 128x8, 64x8), 10, 11 the same with the next planes prefetched (128x8 with 512
+ * threads, 64x4 with 128).  Without pic_autotune a handle uses 0 for Yee and the register-
  * blocked 128x8 (2D) or y-marching 128x4 (3D) tile for customised stencils.  */
 #define PIC_MAX_TILE_VARIANTS 16
 pic_status pic_autotune(pic_t* h, void* stream);

@@ -972,6 +972,90 @@ __global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int 
     if (vec) cp_async_wait_all();                   // no copy may outlive the CTA's shared memory
 }
 
+// Ring variant of the y-march: the planes a step needs next (E^n(k+3), B^n(k+2), J(k+2)) are
+// copied by cp.async while the step computes, into a ring of 4 E, 3 B and 2 J planes.
+template <int MAXM, int TZ, int TX>
+struct MarchRingT {
+    using P = MarchT<MAXM, TZ, TX>;
+    static constexpr size_t smem_bytes = sizeof(float) * 3 * (4 * P::PE + 3 * P::PB + 2 * P::PJ);
+};
+
+template <int MAXM, int TZ, int TX, int NT>
+__global__ void __launch_bounds__(NT) field_advance_march_ring_kernel(FieldP p, int yc) {
+    using T = MarchT<MAXM, TZ, TX>;
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const GridP& g = p.g;
+    const long long N = g.ncell;
+    const bool vec = p.vec4 != 0;
+    const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TX;
+    const int ya = blockIdx.z * yc, yb = min(ya + yc, g.ny);
+    auto Eslot = [&](int i) { return sm + i * 3 * T::PE; };
+    auto Bslot = [&](int i) { return sm + 12 * T::PE + i * 3 * T::PB; };
+    auto Jslot = [&](int i) { return sm + 12 * T::PE + 9 * T::PB + i * 3 * T::PJ; };
+    auto stageE = [&](int i, int y) {
+        stage_plane(Eslot(i), T::PE, p.Ein, p.Ein + N, p.Ein + 2 * N, T::RX0, T::WE, z0 - T::H0, x0, -1,
+                    wrapi(y, g.ny), g, vec);
+    };
+    auto stageB = [&](int i, int y) {
+        stage_plane(Bslot(i), T::PB, p.Bin, p.Bin + N, p.Bin + 2 * N, T::RX1, T::WB, z0 - T::H1, x0, -1,
+                    wrapi(y, g.ny), g, vec);
+    };
+    auto stageJ = [&](int i, int y) {
+        stage_plane(Jslot(i), T::PJ, p.J1, p.J2, p.J3, T::RX2, T::WJ, z0 - T::H2, x0, 0, wrapi(y, g.ny), g, vec);
+    };
+    // prologue: B^{n+1/2}(ya-1), B^{n+1/2}(ya), E^{n+1}(ya), then the first prefetch
+    stageE(0, ya - 1);
+    stageE(1, ya);
+    stageE(2, ya + 1);
+    stageB(0, ya - 1);
+    stageB(1, ya);
+    stageJ(0, ya);
+    if (vec) cp_async_wait_all();
+    __syncthreads();
+    march_bhalf<MAXM, TZ, TX>(p, Bslot(0), Eslot(0), Eslot(1), z0);
+    march_bhalf<MAXM, TZ, TX>(p, Bslot(1), Eslot(1), Eslot(2), z0);
+    __syncthreads();
+    march_enew<MAXM, TZ, TX>(p, Eslot(1), Bslot(1), Bslot(0), Jslot(0), z0);
+    __syncthreads();
+    // E: ec = E^{n+1}(k), en = E^n(k+1), ef = E^n(k+2) (in flight), eg = free
+    // B: bc = B^{n+1/2}(k), bf = B^n(k+1) (in flight), bg = free;  J: jf = J(k+1) (in flight), jg = free
+    int ec = 1, en = 2, ef = 3, eg = 0, bc = 1, bf = 2, bg = 0, jf = 1, jg = 0;
+    stageE(ef, ya + 2);
+    stageB(bf, ya + 1);
+    stageJ(jf, ya + 1);
+    if (vec) cp_async_commit_group();
+    for (int k = ya; k < yb; ++k) {
+        stageE(eg, k + 3);
+        stageB(bg, k + 2);
+        stageJ(jg, k + 2);
+        if (vec) {
+            cp_async_commit_group();
+            cp_async_wait_prev_group();             // this step's planes (committed one step earlier)
+        }
+        __syncthreads();
+        march_bhalf<MAXM, TZ, TX>(p, Bslot(bf), Eslot(en), Eslot(ef), z0);
+        __syncthreads();
+        march_enew<MAXM, TZ, TX>(p, Eslot(en), Bslot(bf), Bslot(bc), Jslot(jf), z0);
+        __syncthreads();
+        march_bnew_store<MAXM, TZ, TX>(p, Eslot(ec), Eslot(en), Bslot(bc), z0, x0, k, vec);
+        __syncthreads();
+        int t = ec;
+        ec = en;
+        en = ef;
+        ef = eg;
+        eg = t;
+        t = bc;
+        bc = bf;
+        bf = bg;
+        bg = t;
+        t = jf;
+        jf = jg;
+        jg = t;
+    }
+    if (vec) cp_async_wait_all();
+}
+
 template <int MAXM, int TZ, int TX, int NT>
 __global__ void __launch_bounds__(NT) field_advance_march_kernel(FieldP p, int yc) {
     using T = MarchT<MAXM, TZ, TX>;
@@ -1157,6 +1241,32 @@ cudaError_t launch_fa_march2(const FieldP& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int MAXM, int TZ, int TX, int NT>
+cudaError_t launch_fa_march_ring(const FieldP& p, cudaStream_t s) {
+    using T = MarchRingT<MAXM, TZ, TX>;
+    auto k = field_advance_march_ring_kernel<MAXM, TZ, TX, NT>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    // y chunks: one wave of CTAs, each chunk at least 8 planes
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int cols = ((p.g.nz + TZ - 1) / TZ) * ((p.g.nx + TX - 1) / TX);
+    int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2048 / NT ? 2048 / NT : per_sm);
+    int chunks = (int)(((long long)nsm * per_sm + cols - 1) / cols);
+    chunks = chunks < 1 ? 1 : chunks;
+    int yc = (p.g.ny + chunks - 1) / chunks;
+    yc = yc < 8 ? 8 : yc;
+    dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, (p.g.ny + yc - 1) / yc);
+    k<<<grid, NT, T::smem_bytes, s>>>(p, yc);
+    return cudaGetLastError();
+}
+
 // In-place Sec. 3 correction J1[i] <- sum_{|m| <= hlen} h[m] J1[i - m] along z (J1 = 0 outside
 // 0 <= i < nz).  One CTA holds a whole z row in shared memory, so no other CTA reads the values
 // it overwrites.  Each thread produces four consecutive outputs from the (2 PIC_MAX_HLEN + 4)-float
@@ -1274,8 +1384,9 @@ cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_row
 //   3D: 0 = 64 x 4 x 4, 1 = 128 x 4 x 2, 2 = 32 x 8 x 4,
 //       3 = rb 64 x 4 x 4, 4 = rb 128 x 4 x 2, 5 = rb 32 x 8 x 4,
 //       6 = y-march 128 x 4 (256 threads), 7 = y-march 128 x 4 (128 threads),
-//       8 = y-march 128 x 8 (256 threads), 9 = y-march 64 x 8 (256 threads)
-int field_variants(int ndim) { return ndim == 2 ? 12 : 10; }
+//       8 = y-march 128 x 8 (256 threads), 9 = y-march 64 x 8 (256 threads),
+//       10 = y-march with prefetch ring 128 x 8 (512 threads), 11 = ring 64 x 4 (128 threads)
+int field_variants(int ndim) { return ndim == 2 ? 12 : 12; }
 
 // Variant used before (or without) pic_autotune: the register-blocked tile for the customised
 // stencils, the scalar tile for Yee.
@@ -1313,6 +1424,8 @@ cudaError_t launch_fa_variant(const FieldP& p, int v, cudaStream_t s) {
         case 7: return launch_fa_march<MAXM, 128, 4, 128>(p, s);
         case 8: return launch_fa_march<MAXM, 128, 8, 256>(p, s);
         case 9: return launch_fa_march<MAXM, 64, 8, 256>(p, s);
+        case 10: return launch_fa_march_ring<MAXM, 128, 8, 512>(p, s);
+        case 11: return launch_fa_march_ring<MAXM, 64, 4, 128>(p, s);
         default: return launch_fa<3, MAXM, 64, 4, 4>(p, s);
     }
 }

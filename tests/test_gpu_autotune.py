@@ -79,7 +79,7 @@ def test_every_tile_variant_matches_oracle(nd, nz, nx, ny, solver, C, moving):
         assert osim.shifts >= 1
     sim = gpu_sim(grid, [], coef=C)
     nv = len(pic_get_tuning(sim.h)[1])
-    assert nv == (12 if nd == 2 else 10)
+    assert nv == (12 if nd == 2 else 12)
     sim.close()
     for v in range(nv):
         sim = gpu_sim(grid, [], coef=C)
