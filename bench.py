@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--small", action="store_true", help="reduced grid (profiling captures)")
     ap.add_argument("--fields-case", default=None, choices=["2d_yee", "2d_custom16", "3d_custom16"],
                     help="fields workload: run this grid only (profiling captures)")
+    ap.add_argument("--sort-every", type=int, default=20, help="steps between particle sorts")
     ap.add_argument("--tile", type=int, default=None,
                     help="fields workload: force this field-advance tile variant instead of autotuning")
     ap.add_argument("--workload", default="beam2d", choices=["beam2d", "beam3d", "batch", "fields"],
@@ -250,7 +251,7 @@ def run_ours(args, rank, world, local_rank):
     cap_extra = 200_000 if nd == 2 else 4_000_000    # injection between two compacting sorts
     kw = {k: grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape", "solver",
                                "moving_window", "inject_species", "inject_ppc", "rho_bg")}
-    sim = Simulation(device=str(dev), sort_every=20, **kw)
+    sim = Simulation(device=str(dev), sort_every=args.sort_every, **kw)
     for s, sp in enumerate(sps):
         sim.add_species(s, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"],
                         cap=n0[s] + cap_extra)
@@ -358,7 +359,7 @@ def run_ours(args, rank, world, local_rank):
               "config": {"workload": wname,
                          "grid": [grid["nz"], grid["nx"]] + ([grid["ny"]] if nd == 3 else []),
                          "particles": int(sum(n0)), "solver": "custom M=16",
-                         "shape": "quadratic", "moving_window": True, "sort_every": 20,
+                         "shape": "quadratic", "moving_window": True, "sort_every": args.sort_every,
                          "l2": f"inputs larger than L2 (working set {working:.0f} MB > 129 MB)",
                          "parallelism": f"{world} independent replica(s)",
                          "field_tile_variant": int(tuned[0])},

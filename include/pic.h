@@ -248,7 +248,7 @@ pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const floa
  * blocked, 6..9 register-blocked columns that march along y (z x x = 128x4 with 256 or 128
  * threads, 128x8, 64x8), 10, 11 the same with the next planes prefetched (128x8 with 512
  * threads, 64x4 with 128).  Without pic_autotune a handle uses 0 for Yee and the register-
- * blocked 128x8 (2D) or y-marching 128x4 (3D) tile for customised stencils.  */
+ * blocked 128x8 (2D) or y-marching prefetch-ring 128x8 (3D) tile for customised stencils.  */
 #define PIC_MAX_TILE_VARIANTS 16
 pic_status pic_autotune(pic_t* h, void* stream);
 pic_status pic_get_tuning(const pic_t* h, int* variant, double* ms, int* nvariants);

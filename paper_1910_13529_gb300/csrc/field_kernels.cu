@@ -1392,7 +1392,7 @@ int field_variants(int ndim) { return ndim == 2 ? 12 : 12; }
 // stencils, the scalar tile for Yee.
 int default_field_variant(int ndim, int M) {
     if (M <= 1) return 0;
-    return ndim == 2 ? 4 : 6;
+    return ndim == 2 ? 4 : 10;
 }
 
 namespace {
