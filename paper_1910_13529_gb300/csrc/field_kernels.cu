@@ -38,7 +38,12 @@ struct Tile {
     static constexpr size_t smem_bytes = sizeof(float) * 3 * (SE + SB);
 };
 
+// periodic index: a mod n in [0, n); an integer division only when a lies more than one period
+// outside (grids narrower than a tile)
 __device__ __forceinline__ int wrapi(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;
+    if (a < 0 && a >= -n) return a + n;
+    if (a >= n && a - n < n) return a - n;
     a %= n;
     return a < 0 ? a + n : a;
 }
