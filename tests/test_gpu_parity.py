@@ -257,6 +257,29 @@ def test_sort_keeps_particles_and_orders_cells():
     sim.close()
 
 
+def test_sort_orders_3d_cells_in_cubic_tiles():
+    grid = grid_of(3, 40, 12, 10, "yee", 2)
+    sp = wl.random_particles(3, 40, 12, 10, 6000, seed=14, u_scale=1.0, margin=2)
+    sim = gpu_sim(grid, [sp])
+    sim.step(3)
+    before = gpu_particles(sim, 0, 3)
+    sim.sort()
+    p = sim.particles(0)
+    assert len(p["cell"]) == len(before[0]) and np.all(p["cell"] >= 0)
+    iz, ix, iy = decode_cells(p["cell"], sim.nz, sim.nx)
+    izg = iz + 1
+    ntz, ntx = (sim.nz + 2 + 3) // 4, (sim.nx + 3) // 4
+    tile = ((iy // 4) * ntx + ix // 4) * ntz + izg // 4             # 4 x 4 x 4 tiles, z-fastest
+    assert np.all(np.diff(tile) >= 0)
+    inner = ((iy % 4) * 4 + ix % 4) * 4 + izg % 4
+    same = np.diff(tile) == 0
+    assert np.all(np.diff(inner)[same] >= 0)
+    after = gpu_particles(sim, 0, 3)
+    assert np.array_equal(before[0], after[0])
+    assert np.array_equal(before[1], after[1]) and np.array_equal(before[2], after[2])
+    sim.close()
+
+
 def test_sorted_run_matches_oracle():
     grid = grid_of(2, 200, 16, 1, "yee", 2)
     sp = wl.random_particles(2, 200, 16, 1, 4000, seed=9, u_scale=1.0, u_drift=(2.0, 0, 0), margin=20)
