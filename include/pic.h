@@ -153,8 +153,9 @@ pic_status pic_gather_push(pic_t* h, void* stream);
 pic_status pic_deposit(pic_t* h, void* stream);
 pic_status pic_field_advance(pic_t* h, void* stream);
 pic_status pic_step(pic_t* h, int nsteps, void* stream);
-/* Counting sort of every species (dead slots removed; ids follow their particles).  Order: 8 x 8
- * tiles of (z, x) cells, tiles z-fastest then x (then y), cells z-fastest inside a tile. */
+/* Counting sort of every species (dead slots removed; ids follow their particles).  Order: tiles
+ * of 8 x 8 (z, x) cells in 2D and 4 x 4 x 4 (z, x, y) cells in 3D, tiles z-fastest then x then
+ * y, cells z-fastest then x then y inside a tile. */
 pic_status pic_sort(pic_t* h, void* stream);
 
 /* ---- diagnostics (FP64 on the GPU) ----------------------------------------------------
