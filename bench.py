@@ -183,14 +183,25 @@ def captured_traffic(kind, ndim):
     md, src = (os.path.join(ROOT, q) for q in entry)
     try:
         text = open(md).read()
-        digest = hashlib.sha1(open(src, "rb").read()).hexdigest()
+        digest = code_sha1(open(src).read())
     except OSError:
         return None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    h = re.search(r"source_sha1:\s*([0-9a-f]{40})", text)
+    h = re.search(r"code_sha1:\s*([0-9a-f]{40})", text)
     if not m or not h or h.group(1) != digest:
         return None
     return float(m.group(1))
+
+
+def code_sha1(source):
+    """SHA-1 of a C++/CUDA source with its comments and white space removed: a capture stays
+    valid across comment edits and is voided by any change to the code itself."""
+    import hashlib
+    import re
+    code = re.sub(r"/\*.*?\*/", "", source, flags=re.S)
+    code = re.sub(r"//[^\n]*", "", code)
+    code = re.sub(r"\s+", "", code)
+    return hashlib.sha1(code.encode()).hexdigest()
 
 
 def aggregate(ms, pushes_per_step, steps, world, device=None):

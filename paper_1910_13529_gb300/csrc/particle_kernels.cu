@@ -493,9 +493,10 @@ constexpr int FUSED_T = 256;
 //       J1(a,b) = f1 Cz[a] Tx[b],  J2(a,b) = f2 Tz[a] Cx[b],
 //       J3(a,b) = qv v3 (S0z[a] (S0x[b] + dSx[b]/2) + dSz[a] (S0x[b]/2 + dSx[b]/3)),
 //     with Cz = cumsum dSz, Tx = S0x + dSx/2 (and z <-> x);
-//  3. lanes whose deposition windows start at the same node (runs of a cell-sorted warp) add
-//     their contributions with a segmented warp reduction first, so that only one lane per run
-//     issues the shared-memory atomic (dense beams otherwise serialise on the same addresses).
+//  3. the chunk's current is summed in a shared-memory box in 32-bit fixed point (native
+//     integer atomics); when more than 8 lanes of a warp share a deposition window (dense
+//     beams) runs of consecutive lanes are summed by a segmented warp reduction first, so that
+//     one lane per run issues the atomic; the box is added to J with float4 atomics.
 // Boxes larger than the shared-memory caps fall back to global loads / global atomics.
 constexpr int F_CAP = 6 * 1024;    // field box floats (6 components)
 constexpr int J_CAP = 3 * 1024;    // current box floats (3 components)
@@ -1160,6 +1161,8 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
                 ok ? (((unsigned long long)(bz + 4) << 40) | ((unsigned long long)(bx + 4) << 20) |
                       (unsigned long long)(by + 4))
                    : (0xFFFFF00000000000ull | (unsigned)threadIdx.x);
+            // direct atomics when at most 4 lanes share a window (144 deposits per particle make
+            // conflicts costlier than in 2D), else sums over runs of lanes first
             const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
             int* s0 = iJ + ((by - jy0) * jxl + (bx - jx0)) * jzl + (bz - jz0);
             const float MAGIC = 12582912.f;           // 1.5 2^23
