@@ -280,6 +280,35 @@ def test_sort_orders_3d_cells_in_cubic_tiles():
     sim.close()
 
 
+@pytest.mark.parametrize("shape,solver,C", [(1, "yee", None), (2, "custom", TABLE1)])
+def test_switch_point_offsets_and_seam(shape, solver, C):
+    """Particles at the offsets where the shape supports switch nodes (0, 1/4, 1/2, 3/4 and the
+    largest FP32 below 1), in the first and last x columns so that their stencils and moves cross
+    the periodic seam, with momenta along and against z and x; 12 steps against the oracle."""
+    nz, nx = 96, 12
+    grid = grid_of(2, nz, nx, 1, solver, shape, C=C)
+    offs = np.array([0.0, 0.25, 0.5, 0.75, np.nextafter(np.float32(1), np.float32(0))], np.float32)
+    oz, ox = np.meshgrid(offs, offs, indexing="ij")
+    oz, ox = oz.ravel(), ox.ravel()
+    k = len(oz)
+    iz = np.repeat(np.arange(30, 30 + 4 * 6, 6), k)[: 4 * k]
+    ix = np.tile(np.concatenate([np.zeros(k, np.int64), np.full(k, nx - 1, np.int64)]), 2)
+    off = np.stack([np.tile(oz, 4), np.tile(ox, 4)])
+    rng = np.random.default_rng(17)
+    u = rng.normal(size=(3, 4 * k)).astype(np.float32) * 0.8
+    u[1, : 2 * k] = np.abs(u[1, : 2 * k]) * np.where(ix[: 2 * k] == 0, -1.0, 1.0)   # towards the seam
+    sp = wl.species(iz, ix, np.zeros_like(iz), off, u, -1.0, 1.0, 0.05)
+    sim = gpu_sim(grid, [sp], coef=C)
+    osim = oracle_sim(grid, [sp], coef=C)
+    for _ in range(12):
+        sim.step(1)
+        osim.step()
+    assert field_error(sim, osim) < TOL
+    dx, du = particle_errors(sim, osim, 0, 2)
+    assert dx < TOL and du < TOL
+    sim.close()
+
+
 def test_sorted_run_matches_oracle():
     grid = grid_of(2, 200, 16, 1, "yee", 2)
     sp = wl.random_particles(2, 200, 16, 1, 4000, seed=9, u_scale=1.0, u_drift=(2.0, 0, 0), margin=20)
