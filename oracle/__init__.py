@@ -8,14 +8,16 @@ two share no code.
 
 Modules:
   pic_oracle.c  the PIC step in plain C loops (field advance, gather, Boris,
-                Esirkepov deposit, current correction, Gauss residual, window)
+                Esirkepov deposit, current filter, current correction, Gauss
+                residual, window)
   core.py       ctypes wrappers and the step driver (Sim)
   fit.py        Appendix C coefficient fit, Sec. 3 current-correction kernel, CFL
-  kspace.py     Sec. 2-3 k-space integrals: self-force, kappa_r, on-axis E1,
-                Appendix D closed forms
+  kspace.py     Sec. 2-3 k-space integrals: self-force (with and without the current
+                filter), kappa_r, on-axis E1, Appendix D closed forms
 
 Pins (tests/test_oracle_*.py): plane-wave dispersion of Eq. wave, Gauss's law kept
 to round-off, Esirkepov continuity, Boris closed forms, dense-matrix brute force on
 8x8 grids, Table 1 re-fit, the self-force and kappa_r values of Sec. 2-3.
-Parity unpinned: the 5-pass filter is not defined in the paper and is not built.
+The 5-pass current filter (named, not defined, in the paper) is pinned through its k-space
+symbol to the three filtered self-forces of Table 2.
 """

@@ -7,7 +7,8 @@ The step follows the order of the PIC loop in Sec. 1 (deposit -> solve -> interp
 -> push, started at the interpolation so that E and B sit at integer times):
 
     gather E^n, B^n at x^n -> Boris u^{n-1/2} -> u^{n+1/2} -> x^{n+1}
-    -> Esirkepov J^{n+1/2} (x^n -> x^{n+1}) -> [customised] J1 <- h * J1 (Sec. 3)
+    -> Esirkepov J^{n+1/2} (x^n -> x^{n+1}) -> [filter] J <- F J along z
+    -> [customised] J1 <- h * J1 (Sec. 3)
     -> B^{n+1/2}, E^{n+1}, B^{n+1} (Eq. 1) -> drop particles outside 0 <= z < nz
     -> [moving window] shift one cell when n dt >= (s+1) dz, inject cold plasma.
 """
@@ -39,6 +40,7 @@ def lib():
         L.or_rho.argtypes = [_ip, _dp, ctypes.c_long, _dp, ctypes.c_double, _dp]
         L.or_gauss.argtypes = [_ip, _dp, _dp, _dp, _dp, _dp]
         L.or_shift_z.argtypes = [_ip, ctypes.c_int, _dp]
+        L.or_filter_z.argtypes = [_ip, ctypes.c_int, _dp]
     return _lib
 
 
@@ -128,6 +130,13 @@ def shift_z(g: Grid, F):
     lib().or_shift_z(g.ip, F.shape[0], _d(F))
 
 
+def filter_z(g: Grid, F):
+    """The 5-pass current filter along z, in place, on every leading component of F
+    (F of shape (ncomp, ny, nx, nz) or a single (ny, nx, nz) array)."""
+    ncomp = F.shape[0] if F.ndim == 4 else 1
+    lib().or_filter_z(g.ip, ncomp, _d(F))
+
+
 class Species:
     """Macro-particles of one species: positions xi (n,3) in cell units, momenta u = gamma v (n,3)."""
 
@@ -150,8 +159,9 @@ class Species:
 class Sim:
     """Plain FP64 PIC loop over the C oracle routines (one grid, several species)."""
 
-    def __init__(self, g: Grid, species, h=None, moving_window=False, inject=None):
+    def __init__(self, g: Grid, species, h=None, moving_window=False, inject=None, filt=False):
         self.g = g
+        self.filt = bool(filt)
         self.E = g.zeros()
         self.B = g.zeros()
         self.J = g.zeros()
@@ -172,6 +182,8 @@ class Sim:
             xi1 = move(g, sp.xi, sp.u)
             deposit(g, sp.xi, xi1, sp.u, sp.Q, self.J)
             sp.xi = xi1
+        if self.filt:
+            filter_z(g, self.J)
         if self.h is not None:
             correct_j1(g, self.h, self.J)
         field_advance(g, self.E, self.B, self.J)
@@ -212,7 +224,11 @@ class Sim:
         return r
 
     def gauss(self):
-        return gauss(self.g, self.E, self.rho())
+        # with the current filter the field advance keeps Gauss's law for the filtered charge
+        r = self.rho()
+        if self.filt:
+            filter_z(self.g, r)
+        return gauss(self.g, self.E, r)
 
     def field_energy(self):
         return 0.5 * (np.sum(self.E ** 2) + np.sum(self.B ** 2)) * self.g.cell_volume()

@@ -9,6 +9,12 @@ In these units [k1]_t dx1/2 = kappa sin(khat/kappa) and the Yee [k]_1 dx1/2 = si
 Shapes in k space (Sec. 2.1): linear S = (sin khat/khat)^2; quadratic S = (sin khat/khat)^3
 (the B-spline of one order higher; the paper names only the linear form).
 All forces are in units of q^2/dx1, fields in units of q/dx1.
+
+Current filter (Sec. 2.2, 2.3, Table 2: "5 pass filter", not defined in the paper).  Reading:
+four passes of the binomial smoother (1/4, 1/2, 1/4) and one compensating pass (-5/4, 7/2, -5/4)
+along x1.  A symmetric three-point pass (w1, w0, w1) multiplies the grid mode khat by
+w0 + 2 w1 cos(2 khat).  The filter acts on the grid current, i.e. at the fundamental-zone
+wavenumber khat of each integrand; with it the three filtered self-forces of Table 2 follow.
 """
 import math
 
@@ -53,50 +59,73 @@ def kappa_r_custom():
     return optimize.brentq(f, 2.0 + 1e-9, 10.0)
 
 
+# ------------------------------------------------------------------- filter ---
+
+FILTER_PASSES = ((0.25, 0.5),) * 4 + ((-1.25, 3.5),)   # (w1, w0) of each pass, in order
+
+
+def filter_symbol(khat):
+    """Product over the passes of w0 + 2 w1 cos(2 khat) (khat = k1 dx1/2)."""
+    out = 1.0
+    for w1, w0 in FILTER_PASSES:
+        out = out * (w0 + 2.0 * w1 * np.cos(2.0 * np.asarray(khat, dtype=np.float64)))
+    return out
+
+
+def _filt(flag):
+    return (lambda k: float(filter_symbol(k))) if flag else (lambda k: 1.0)
+
+
 # ---------------------------------------------------------------- self-forces ---
 
 def _root(f, a, b):
     return optimize.brentq(f, a, b, xtol=1e-15, rtol=1e-15, maxiter=500)
 
 
-def self_force_yee(kappa=4.0, r=1.0, order=1):
+def self_force_yee(kappa=4.0, r=1.0, order=1, filt=False):
     """Sec. 2.2 (fundamental zone, Cerenkov part):
     F1 = -(1/pi) int_0^{khat_r} S^2/sin(khat) sqrt(D/(1 - r^2 D)) dkhat,
-    D = kappa^2 sin^2(khat/kappa) - sin^2(khat), khat_r: D = r^-2."""
+    D = kappa^2 sin^2(khat/kappa) - sin^2(khat), khat_r: D = r^-2.
+    filt: the integrand carries the current filter's symbol at khat."""
+    Fk = _filt(filt)
     D = lambda k: kt(k, kappa) ** 2 - math.sin(k) ** 2
     g = lambda k: D(k) - r ** -2
     kr = _root(g, 1e-6, math.pi / 2) if g(math.pi / 2) > 0 else math.pi / 2
-    f = lambda k: shape_k(k, order) ** 2 / math.sin(k) * math.sqrt(max(D(k), 0.0) / (1.0 - r * r * D(k)))
+    f = lambda k: Fk(k) * shape_k(k, order) ** 2 / math.sin(k) * math.sqrt(max(D(k), 0.0) / (1.0 - r * r * D(k)))
     val, _ = integrate.quad(f, 0.0, kr, limit=400, epsabs=1e-13, epsrel=1e-12)
     return -val / math.pi
 
 
-def self_force_spectral(kappa=4.0, r=1.0, order=1):
+def self_force_spectral(kappa=4.0, r=1.0, order=1, filt=False):
     """Sec. 2.3 (first aliasing zones, Cerenkov part):
     F1 = -(1/pi) int_{-khat_r1}^{-khat_r2} S(khat) S(khat+pi)/khat sqrt([khat+pi]_t^2 - khat^2) dkhat,
-    [-khat_r1+pi]_t^2 = khat_r1^2,  [-khat_r2+pi]_t^2 - khat_r2^2 = (pi/(2r))^2."""
+    [-khat_r1+pi]_t^2 = khat_r1^2,  [-khat_r2+pi]_t^2 - khat_r2^2 = (pi/(2r))^2.
+    filt: the integrand carries the current filter's symbol at khat."""
+    Fk = _filt(filt)
     X = lambda k: kt(k + math.pi, kappa) ** 2 - k * k
     r1 = -_root(lambda k: X(k), -math.pi / 2, -1e-9) if X(-math.pi / 2) < 0 else math.pi / 2
     r2 = -_root(lambda k: X(k) - (math.pi / (2 * r)) ** 2, -r1, -1e-9)
-    f = lambda k: shape_k(k, order) * shape_k(k + math.pi, order) / k * math.sqrt(max(X(k), 0.0))
-    val, _ = integrate.quad(f, -r1, -r2, limit=400, epsabs=1e-14, epsrel=1e-12)
+    f = lambda k: Fk(k) * shape_k(k, order) * shape_k(k + math.pi, order) / k * math.sqrt(max(X(k), 0.0))
+    val, _ = integrate.quad(f, -r1, -r2, limit=400, epsabs=0.0, epsrel=1e-10)
     return -val / math.pi
 
 
-def self_force_custom(kappa=4.0, r=1.0, order=1, printed=False):
+def self_force_custom(kappa=4.0, r=1.0, order=1, printed=False, filt=False):
     """Sec. 3, solver with [k]_1 = [k1]_t (first aliasing zones, Cerenkov part):
     F1 = -(1/pi) int_{-pi/2}^{-khat_r} S(khat) S(khat+pi) / K(khat) sqrt(X/(1 - r^2 X)) dkhat,
     X = [khat+pi]_t^2 - [khat]_t^2, khat_r: X = r^-2.
 
     Eq. E12D divides by [k]_B1 = [k1]_t, i.e. K = kappa sin(khat/kappa) in khat units
     (printed=False).  The Sec. 3 closed form prints K = sin(khat/kappa) (printed=True); that
-    form is kappa times larger and is the one that reproduces the printed 0.040 / 0.016."""
+    form is kappa times larger and is the one that reproduces the printed 0.040 / 0.016.
+    filt: the integrand carries the current filter's symbol at khat."""
+    Fk = _filt(filt)
     X = lambda k: kt(k + math.pi, kappa) ** 2 - kt(k, kappa) ** 2
     kr = -_root(lambda k: X(k) - r ** -2, -math.pi / 2 + 1e-12, math.pi / 2)
     K = (lambda k: math.sin(k / kappa)) if printed else (lambda k: kt(k, kappa))
-    f = lambda k: (shape_k(k, order) * shape_k(k + math.pi, order) / K(k)
+    f = lambda k: (Fk(k) * shape_k(k, order) * shape_k(k + math.pi, order) / K(k)
                    * math.sqrt(max(X(k), 0.0) / (1.0 - r * r * X(k))))
-    val, _ = integrate.quad(f, -math.pi / 2, -kr, limit=400, epsabs=1e-15, epsrel=1e-12)
+    val, _ = integrate.quad(f, -math.pi / 2, -kr, limit=400, epsabs=0.0, epsrel=1e-10)
     return -val / math.pi
 
 

@@ -23,6 +23,8 @@
  *   - Current correction for the customised stencil (Sec. 3): J1 <- h * J1
  *     along z, h the impulse response of the inverse of the symbol ratio
  *     P = [k]_custom / [k]_Yee; h is supplied by the caller.
+ *   - Current filter along z (the "5 pass" filter the paper uses with its runs and
+ *     Table 2): four binomial passes and one compensating pass, on every current component.
  *   - Gauss residual d-.E - rho (Eq. Gauss), charge density, energies.
  *
  * Grid conventions.  Axis 1 is z (index i, contiguous), axis 2 is x (index j),
@@ -375,6 +377,36 @@ void or_gauss(const int* ip, const double* dp, const double* C, const double* E,
                 long c = lin(&g, i, j, k);
                 G[c] = dzm(&g, E, i, j, k) + dxm(&g, E + N, i, j, k) + dym(&g, E + 2 * N, i, j, k) - rho[c];
             }
+}
+
+/* Current filter along z (the "5 pass" filter of Sec. 2.2, 2.3 and Table 2; the paper names it
+ * without defining it).  Reading: four passes of the binomial smoother (1/4, 1/2, 1/4) followed
+ * by one compensating pass (-5/4, 7/2, -5/4).  Each pass is y_i = w1 (x_{i-1} + x_{i+1}) + w0 x_i
+ * over 0 <= i < nz with x = 0 outside that range (open z) or x periodic in z when periodic_z.
+ * The k-space symbol of one pass is w0 + 2 w1 cos(k dz), so the whole filter multiplies a
+ * Fourier mode by cos^8(k dz/2) (1 + 5 sin^2(k dz/2)).  ncomp arrays of nz*nx*ny doubles. */
+void or_filter_z(const int* ip, int ncomp, double* F) {
+    static const double w1[5] = {0.25, 0.25, 0.25, 0.25, -1.25};
+    static const double w0[5] = {0.5, 0.5, 0.5, 0.5, 3.5};
+    grid_t g = mk(ip, (const double[4]){1, 1, 1, 1}, NULL);
+    long N = ncell(&g);
+    double* x = (double*)malloc(sizeof(double) * g.nz);
+    for (int c = 0; c < ncomp; ++c)
+        for (int k = 0; k < g.ny; ++k)
+            for (int j = 0; j < g.nx; ++j) {
+                double* row = F + c * N + lin(&g, 0, j, k);
+                for (int p = 0; p < 5; ++p) {
+                    memcpy(x, row, sizeof(double) * g.nz);
+                    for (int i = 0; i < g.nz; ++i) {
+                        int il = i - 1, ir = i + 1;
+                        if (g.periodic_z) { il = wrap(il, g.nz); ir = wrap(ir, g.nz); }
+                        double xl = (il >= 0 && il < g.nz) ? x[il] : 0.0;
+                        double xr = (ir >= 0 && ir < g.nz) ? x[ir] : 0.0;
+                        row[i] = w1[p] * (xl + xr) + w0[p] * x[i];
+                    }
+                }
+            }
+    free(x);
 }
 
 /* Moving window: every field array moves one cell towards -z, the front column becomes zero. */

@@ -65,6 +65,25 @@ def test_self_force_custom(order, name):
     assert a / b == pytest.approx(4.0, rel=1e-6)
 
 
+def test_filtered_self_forces_table2():
+    """Table 2 (and Sec. 2.2, 2.3): quadratic shape with the 5-pass current filter.  The filter is
+    not defined in the paper; the reading (four (1,2,1)/4 passes and a (-5/4, 7/2, -5/4)
+    compensator along x1) reproduces all three printed values, one per solver."""
+    check("yee_F1_quadratic_5pass", kspace.self_force_yee(4.0, 1.0, 2, filt=True))
+    check("spectral_F1_quadratic_5pass", kspace.self_force_spectral(4.0, 1.0, 2, filt=True))
+    check("custom_F1_quadratic_5pass", kspace.self_force_custom(4.0, 1.0, 2, printed=True, filt=True))
+
+
+def test_filter_symbol_limits():
+    # DC passes unchanged, the grid Nyquist mode (khat = pi/2) is removed, the symbol stays in [0, 1.1]
+    assert kspace.filter_symbol(0.0) == pytest.approx(1.0, abs=1e-15)
+    assert abs(kspace.filter_symbol(math.pi / 2)) < 1e-15
+    import numpy as np
+    k = np.linspace(0, math.pi / 2, 2001)
+    s = kspace.filter_symbol(k)
+    assert s.min() >= -1e-15 and s.max() < 1.1
+
+
 def test_sign_of_self_forces():
     # Sec. 2.2: Yee decelerates; Sec. 2.3 and Sec. 3: accelerate
     assert kspace.self_force_yee() < 0
