@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--fields-case", default=None, choices=["2d_yee", "2d_custom16", "3d_custom16"],
                     help="fields workload: run this grid only (profiling captures)")
     ap.add_argument("--sort-every", type=int, default=20, help="steps between particle sorts")
+    ap.add_argument("--filter", action="store_true",
+                    help="beam workloads with the 5-pass current filter along z (not the headline run)")
     ap.add_argument("--tile", type=int, default=None,
                     help="fields workload: force this field-advance tile variant instead of autotuning")
     ap.add_argument("--workload", default="beam2d", choices=["beam2d", "beam3d", "batch", "fields"],
@@ -57,7 +59,15 @@ def parse():
 
 
 def workload(args):
-    """(grid, species, name) of the timed run."""
+    """(grid, species, name) of the timed run (with the 5-pass current filter under --filter)."""
+    (grid, sps), name = _workload(args)
+    if getattr(args, "filter", False):
+        grid["current_filter"] = True
+        name += "_filtered"
+    return (grid, sps), name
+
+
+def _workload(args):
     from paper_1910_13529_gb300 import workloads as wl
     if args.workload == "beam3d":
         if args.small:
@@ -152,7 +162,7 @@ def oracle_baseline(grid, sps, frac=0.25, seed=0, steps=2):
         species.append(oc.Species(wl.xi_of(sub, grid["ndim"]), sub["u"].T.astype(np.float64), sp["q"], sp["m"],
                                   sp["w"]))
         n += int(sel.sum())
-    sim = oc.Sim(g, species, h=h, moving_window=True)
+    sim = oc.Sim(g, species, h=h, moving_window=True, filt=grid.get("current_filter", False))
     t0 = time.perf_counter()
     for _ in range(steps):
         sim.step()
@@ -262,6 +272,7 @@ def run_ours(args, rank, world, local_rank):
     cap_extra = 200_000 if nd == 2 else 4_000_000    # injection between two compacting sorts
     kw = {k: grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape", "solver",
                                "moving_window", "inject_species", "inject_ppc", "rho_bg")}
+    kw["current_filter"] = grid.get("current_filter", False)
     sim = Simulation(device=str(dev), sort_every=args.sort_every, **kw)
     for s, sp in enumerate(sps):
         sim.add_species(s, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"],
@@ -371,6 +382,7 @@ def run_ours(args, rank, world, local_rank):
                          "grid": [grid["nz"], grid["nx"]] + ([grid["ny"]] if nd == 3 else []),
                          "particles": int(sum(n0)), "solver": "custom M=16",
                          "shape": "quadratic", "moving_window": True, "sort_every": args.sort_every,
+                         "current_filter": "5-pass" if kw["current_filter"] else "none",
                          "l2": f"inputs larger than L2 (working set {working:.0f} MB > 129 MB)",
                          "parallelism": f"{world} independent replica(s)",
                          "field_tile_variant": int(tuned[0])},

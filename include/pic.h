@@ -8,6 +8,8 @@
  *     2M-point stencil d+/d- of Sec. 3 and Appendix C;
  *   - charge-conserving (Esirkepov) current deposition, which keeps Gauss's law
  *     (Eq. Gauss) as Sec. 2.1 requires, with linear or quadratic B-spline shapes;
+ *   - optionally the current filter along z that the paper runs with ("5 pass filter",
+ *     Sec. 2.2, 2.3, Table 2): four (1/4, 1/2, 1/4) passes and one (-5/4, 7/2, -5/4) pass;
  *   - for the customised stencil, the current correction of Sec. 3: J1 <- h * J1 along z,
  *     h the impulse response of 1/P, P(k) = [k]_custom / [k]_Yee;
  *   - field interpolation (gather) and a relativistic Boris push (leapfrog, Sec. 2.1);
@@ -63,6 +65,15 @@ typedef enum {
 
 enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_CUSTOM = 1 };
 
+/* Current filter along z (pic_config.current_filter).  The paper uses a "5 pass filter" with its
+ * runs and with the self-forces of Table 2 and does not define it; PIC_FILTER_5PASS is the reading
+ * that reproduces all three filtered self-forces of Table 2: four binomial passes
+ * y_i = (x_{i-1} + 2 x_i + x_{i+1}) / 4 and one compensating pass
+ * y_i = (-5 x_{i-1} + 14 x_i - 5 x_{i+1}) / 4, each with x = 0 outside 0 <= i < nz; k-space symbol
+ * cos^8(k dz/2) (1 + 5 sin^2(k dz/2)).  It acts on J1, J2 and J3 after deposition and before the
+ * Sec. 3 correction.                                                                          */
+enum { PIC_FILTER_NONE = 0, PIC_FILTER_5PASS = 1 };
+
 #define PIC_MAX_M 16        /* largest customised stencil (Appendix C uses M = 16) */
 #define PIC_MAX_HLEN 24     /* current-correction taps kept on each side in FP32 */
 #define PIC_MAX_SPECIES 4
@@ -98,6 +109,7 @@ typedef struct pic_config {
     int inject_ppc[3];      /* quiet-start particles per cell along z, x, y for injection */
     double rho_bg;          /* uniform background charge density (Gauss diagnostic only) */
     int sort_every;         /* pic_step sorts particles by cell every sort_every steps (0: never) */
+    int current_filter;     /* PIC_FILTER_NONE or PIC_FILTER_5PASS */
 } pic_config;
 
 /* ---- handle ------------------------------------------------------------------------
@@ -141,8 +153,9 @@ pic_status pic_bind_species(pic_t* h, int s, int32_t* cell, float* off, float* u
  *   E^n, B^n at x^n (shape-weighted, staggered), Boris u^{n-1/2} -> u^{n+1/2}, and move
  *   x^{n+1} = x^n + dt u/gamma; the old position is kept in library scratch.
  * pic_deposit: zero J, deposit J^{n+1/2} from the old and new positions (Esirkepov) for all
- *   species, apply the Sec. 3 correction to J1 (customised stencil), and retire particles
- *   that left 0 <= z < nz.  Requires a preceding pic_gather_push (else PIC_ERR_STATE).
+ *   species, apply the current filter (if configured) to J1, J2, J3 and the Sec. 3 correction
+ *   to J1 (customised stencil), and retire particles that left 0 <= z < nz.  Requires a
+ *   preceding pic_gather_push (else PIC_ERR_STATE).
  * pic_field_advance: B^{n+1/2} = B^n - dt/2 d+xE^n, E^{n+1} = E^n + dt (d-xB^{n+1/2} - J),
  *   B^{n+1} = B^{n+1/2} - dt/2 d+xE^{n+1} (Eq. 1); completes step n.  If the window is due,
  *   the fields are shifted one cell towards -z, the front column zeroed and the injected
@@ -153,6 +166,10 @@ pic_status pic_gather_push(pic_t* h, void* stream);
 pic_status pic_deposit(pic_t* h, void* stream);
 pic_status pic_field_advance(pic_t* h, void* stream);
 pic_status pic_step(pic_t* h, int nsteps, void* stream);
+/* The current filter of PIC_FILTER_5PASS applied once, in place, to the bound J (J1, J2, J3),
+ * whatever cfg.current_filter says; pic_deposit and pic_step run the same kernel after the
+ * deposit when the handle is configured with the filter.  Zero current outside 0 <= i < nz. */
+pic_status pic_filter_current(pic_t* h, void* stream);
 /* Counting sort of every species (dead slots removed; ids follow their particles).  Order: tiles
  * of 8 x 8 (z, x) cells in 2D and 4 x 4 x 4 (z, x, y) cells in 3D, tiles z-fastest then x then
  * y, cells z-fastest then x then y inside a tile. */
@@ -161,7 +178,10 @@ pic_status pic_sort(pic_t* h, void* stream);
 /* ---- diagnostics (FP64 on the GPU) ----------------------------------------------------
  * pic_diag fills out[PIC_DIAG_N] (indices above) and synchronises stream.  The Gauss
  * residual d-.E - rho - rho_bg uses the same d- as Ampere's law (customised stencil
- * included) and skips nodes within (M + hlen + 2) cells of the z ends.                  */
+ * included) and skips nodes within (M + hlen + 2) cells of the z ends (2 for Yee), plus 5
+ * with the current filter.  With the filter, the field advance keeps Gauss's law for the
+ * filtered charge, so pic_diag, pic_gauss and pic_gauss_static filter rho along z the same way
+ * (in FP64) before taking the residual; pic_rho always returns the unfiltered density.    */
 pic_status pic_diag(pic_t* h, double* out, void* stream);
 /* rho (FP64, nz*nx*ny doubles, device) of all live particles at the current positions. */
 pic_status pic_rho(pic_t* h, double* rho, void* stream);
@@ -216,7 +236,8 @@ enum {
     PIC_T_SORT = 4,        /* counting sort */
     PIC_T_WINDOW = 5,      /* injection of the new plasma column */
     PIC_T_DIAG = 6,        /* rho, Gauss residual, reductions */
-    PIC_TIMING_N = 7
+    PIC_T_FILTER = 7,      /* current filter along z */
+    PIC_TIMING_N = 8
 };
 pic_status pic_timing(pic_t* h, int enable);
 pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream);
@@ -228,7 +249,8 @@ pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream
  * dL/dC_l (the Sec. 3 / Appendix C axial coefficients, including their effect through the
  * Sec. 3 current correction) to grad.
  *   E, B:   forward fields at the start of the step (device, 3 nz nx ny floats each);
- *   J:      the (corrected) current of that step, as pic_step / pic_deposit left it in J;
+ *   J:      the (filtered and corrected) current of that step, as pic_step / pic_deposit left
+ *           it in J (the filter precedes the correction and does not depend on C);
  *   aE, aB: device, updated in place; grad: device double[M], accumulated (not cleared).
  * The transposed operators use d-x = (d+x)^T (the pair of Appendix C), so the adjoint step is
  * the leapfrog with the roles of d+ and d- exchanged.  Library scratch: 7 nz nx ny floats.  */
@@ -260,7 +282,7 @@ pic_status pic_set_tuning(pic_t* h, int variant);
  * A batch holds n independent 2D or 3D runs (no moving window, no sort), each with its own
  * grid, dt, stencil (Yee or customised, own coefficients), shape and one particle species.
  * pic_batch_step advances all of them with one launch per kernel class and step (J zero,
- * gather/push/deposit, correction, field advance per stencil class), recorded once into a
+ * gather/push/deposit, filter, correction, field advance per stencil class), recorded once into a
  * CUDA graph (two steps, one per field-buffer parity) and replayed on the caller's stream.
  * Instance i is an ordinary handle (pic_batch_instance) for binding and diagnostics; bind its
  * fields and species before the first pic_batch_step.  After pic_batch_step returns (on the

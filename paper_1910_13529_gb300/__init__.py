@@ -17,6 +17,7 @@ PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_CUDA, PIC_ERR_OOM, PIC_ERR_TIMEOUT, PI
 STATUS_NAMES = ["PIC_OK", "PIC_ERR_ARG", "PIC_ERR_CFL", "PIC_ERR_CUDA", "PIC_ERR_OOM", "PIC_ERR_TIMEOUT",
                 "PIC_ERR_STATE", "PIC_ERR_CAPACITY"]
 PIC_SOLVER_YEE, PIC_SOLVER_CUSTOM = 0, 1
+PIC_FILTER_NONE, PIC_FILTER_5PASS = 0, 1
 PIC_MAX_M, PIC_MAX_HLEN, PIC_MAX_SPECIES, PIC_DIAG_N = 16, 24, 4, 10
 PIC_STATIC_RHO_CELLS = 1 << 20
 DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "count", "step", "shifts",
@@ -25,12 +26,12 @@ DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "co
 # exported symbols declared in include/pic.h
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_correction_taps",
            "pic_cfl_dt", "pic_get_coefficients", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
-           "pic_deposit", "pic_field_advance", "pic_step", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
+           "pic_deposit", "pic_field_advance", "pic_step", "pic_filter_current", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
            "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
            "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy",
            "pic_autotune", "pic_get_tuning", "pic_set_tuning", "pic_adjoint_step",
            "pic_set_state", "pic_get_next_id"]
-TIMING_KEYS = ["particles", "deposit", "correction", "fields", "sort", "window", "diag"]
+TIMING_KEYS = ["particles", "deposit", "correction", "fields", "sort", "window", "diag", "filter"]
 
 
 class PicError(RuntimeError):
@@ -46,7 +47,7 @@ class pic_config(ctypes.Structure):
         ("solver", ctypes.c_int), ("M", ctypes.c_int), ("coef", ctypes.POINTER(ctypes.c_double)),
         ("fit_wk", ctypes.c_double), ("fit_n", ctypes.c_double), ("shape", ctypes.c_int),
         ("moving_window", ctypes.c_int), ("inject_species", ctypes.c_int), ("inject_ppc", ctypes.c_int * 3),
-        ("rho_bg", ctypes.c_double), ("sort_every", ctypes.c_int),
+        ("rho_bg", ctypes.c_double), ("sort_every", ctypes.c_int), ("current_filter", ctypes.c_int),
     ]
 
 
@@ -73,6 +74,7 @@ def _load():
         "pic_field_advance": ([vp, vp], ctypes.c_int),
         "pic_step": ([vp, ctypes.c_int, vp], ctypes.c_int),
         "pic_sort": ([vp, vp], ctypes.c_int),
+        "pic_filter_current": ([vp, vp], ctypes.c_int),
         "pic_diag": ([vp, dp, vp], ctypes.c_int),
         "pic_rho": ([vp, vp, vp], ctypes.c_int),
         "pic_gauss": ([vp, vp, vp], ctypes.c_int),
@@ -195,6 +197,10 @@ def pic_step(h, nsteps, stream):
 
 def pic_sort(h, stream):
     _check(lib.pic_sort(h, stream), h)
+
+
+def pic_filter_current(h, stream):
+    _check(lib.pic_filter_current(h, stream), h)
 
 
 def pic_diag(h, stream):

@@ -308,6 +308,8 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     if (c.solver != PIC_SOLVER_YEE && c.solver != PIC_SOLVER_CUSTOM)
         return fail(nullptr, PIC_ERR_ARG, "unknown solver %d", c.solver);
     if (c.shape != 1 && c.shape != 2) return fail(nullptr, PIC_ERR_ARG, "shape must be 1 or 2");
+    if (c.current_filter != PIC_FILTER_NONE && c.current_filter != PIC_FILTER_5PASS)
+        return fail(nullptr, PIC_ERR_ARG, "unknown current_filter %d", c.current_filter);
     if (c.inject_species >= PIC_MAX_SPECIES) return fail(nullptr, PIC_ERR_ARG, "inject_species out of range");
     if (c.inject_species >= 0 && (c.inject_ppc[0] < 1 || c.inject_ppc[1] < 1 || (c.ndim == 3 && c.inject_ppc[2] < 1)))
         return fail(nullptr, PIC_ERR_ARG, "inject_ppc must be >= 1");
@@ -482,6 +484,10 @@ pic_status pic_deposit(pic_t* h, void* stream) {
         Scope sc(h, PIC_T_DEPOSIT, 1, s);
         CK(h, launch_deposit_unfused(h->g, sp, h->J, h->sp[i].extent, s), "deposit kernel");
     }
+    if (h->cfg.current_filter) {
+        Scope sc(h, PIC_T_FILTER, 1, s);
+        CK(h, launch_filter_current(h->g, h->J, s), "current filter kernel");
+    }
     if (h->hlen > 0) {
         Scope sc(h, PIC_T_CORRECTION, 1, s);
         CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
@@ -528,6 +534,10 @@ pic_status pic_step(pic_t* h, int nsteps, void* stream) {
                "fused push/deposit kernel");
         }
         h->pending_shift = 0;
+        if (h->cfg.current_filter) {
+            Scope sc(h, PIC_T_FILTER, 1, s);
+            CK(h, launch_filter_current(h->g, h->J, s), "current filter kernel");
+        }
         if (h->hlen > 0) {
             Scope sc(h, PIC_T_CORRECTION, 1, s);
             CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
@@ -546,6 +556,16 @@ pic_status pic_step(pic_t* h, int nsteps, void* stream) {
         CK(h, cudaMemcpyAsync(h->B, Bc, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s), "copy B");
     }
     h->state = 0;
+    return PIC_OK;
+}
+
+pic_status pic_filter_current(pic_t* h, void* stream) {
+    if (!h) return PIC_ERR_ARG;
+    pic_status st = need_fields(h);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scope sc(h, PIC_T_FILTER, 1, s);
+    CK(h, launch_filter_current(h->g, h->J, s), "current filter kernel");
     return PIC_OK;
 }
 
@@ -572,6 +592,8 @@ pic_status pic_gauss(pic_t* h, double* G, void* stream) {
     pic_status st = need_fields(h);
     if (st) return st;
     if ((st = pic_rho(h, h->rho64, stream))) return st;
+    if (h->cfg.current_filter)
+        CK(h, launch_filter_rho(h->g, h->rho64, (cudaStream_t)stream), "rho filter kernel");
     CK(h, launch_gauss(h->g, h->st, h->E, h->rho64, h->cfg.rho_bg, G, (cudaStream_t)stream), "gauss kernel");
     return PIC_OK;
 }
@@ -602,6 +624,7 @@ pic_status pic_gauss_static(pic_t* h, double* G, void* stream) {
         SpeciesP sp = species_params(h, i);
         CK(h, launch_rho(h->g, sp, h->pending_shift, rho, h->sp[i].extent, s), "rho kernel");
     }
+    if (h->cfg.current_filter) CK(h, launch_filter_rho(h->g, rho, s), "rho filter kernel");
     CK(h, launch_gauss(h->g, h->st, h->E, rho, h->cfg.rho_bg, G, s), "gauss kernel");
     return PIC_OK;
 }
@@ -613,8 +636,9 @@ pic_status pic_diag(pic_t* h, double* out, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     Scope sc(h, PIC_T_DIAG, 3, s);
     if ((st = pic_rho(h, h->rho64, stream))) return st;
+    if (h->cfg.current_filter) CK(h, launch_filter_rho(h->g, h->rho64, s), "rho filter kernel");
     CK(h, cudaMemsetAsync(h->acc, 0, sizeof(double) * 16, s), "zero accumulators");
-    int margin = h->hlen > 0 ? h->st.M + h->hlen + 2 : 2;
+    int margin = (h->hlen > 0 ? h->st.M + h->hlen + 2 : 2) + (h->cfg.current_filter ? 5 : 0);
     CK(h, launch_diag_reduce(h->g, h->st, h->E, h->B, h->rho64, h->cfg.rho_bg, margin, h->acc, s), "diag kernel");
     for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
         if (!h->sp[i].bound) continue;
@@ -838,6 +862,9 @@ struct pic_batch_t {
     } pg[2];            // shape 1, 2
     CorrInst* d_corr = nullptr;
     int ncorr = 0, max_rows = 0, max_nz = 0;
+    FiltInst* d_filt = nullptr;
+    int nfilt = 0;
+    long long max_rows3 = 0;
     int ndim = 2;
     bool built = false;
     cudaStream_t cap = nullptr;
@@ -870,12 +897,22 @@ pic_status batch_build(pic_batch_t* b) {
     for (auto& f : b->fg) f.members.clear();
     for (auto& q : b->pg) q.members.clear();
     std::vector<CorrInst> corr;
+    std::vector<FiltInst> filt;
     b->max_rows = b->max_nz = 0;
+    b->max_rows3 = 0;
     for (int i = 0; i < (int)b->h.size(); ++i) {
         pic_t* h = b->h[i];
         if (!h->E || !h->sp[0].bound) return bfail(b, PIC_ERR_STATE, "batch instance not bound (fields and species 0)");
         b->fg[stencil_class(h->st.M)].members.push_back(i);
         b->pg[h->cfg.shape - 1].members.push_back(i);
+        if (h->cfg.current_filter) {
+            FiltInst f;
+            f.g = h->g;
+            f.J = h->J;
+            f.vec4 = filter_vec4_ok(h->J, h->g.nz) ? 1 : 0;
+            filt.push_back(f);
+            b->max_rows3 = std::max(b->max_rows3, 3LL * h->g.nx * h->g.ny);
+        }
         if (h->hlen > 0) {
             CorrInst c;
             c.g = h->g;
@@ -942,6 +979,8 @@ pic_status batch_build(pic_batch_t* b) {
     }
     b->ncorr = (int)corr.size();
     if (upload(&b->d_corr, corr) != cudaSuccess) return bfail(b, PIC_ERR_OOM, "batch correction table");
+    b->nfilt = (int)filt.size();
+    if (upload(&b->d_filt, filt) != cudaSuccess) return bfail(b, PIC_ERR_OOM, "batch filter table");
     b->built = true;
     return PIC_OK;
 }
@@ -955,6 +994,7 @@ cudaError_t batch_enqueue_step(pic_batch_t* b, int parity, cudaStream_t s) {
         if (!q.members.empty() &&
             (e = launch_push_batch(q.d_inst, (int)q.members.size(), b->ndim, q.shape, q.max_extent, parity, s)))
             return e;
+    if (b->nfilt && (e = launch_filter_current_batch(b->d_filt, b->nfilt, b->max_rows3, s))) return e;
     if (b->ncorr && (e = launch_correct_j1_batch(b->d_corr, b->ncorr, b->max_rows, b->max_nz, s))) return e;
     for (auto& f : b->fg)
         if (!f.members.empty() &&
@@ -1057,6 +1097,7 @@ pic_status pic_batch_destroy(pic_batch_t* b) {
     }
     for (auto& q : b->pg) dfree(q.d_inst);
     dfree(b->d_corr);
+    dfree(b->d_filt);
     for (pic_t* h : b->h) pic_destroy(h);
     delete b;
     return PIC_OK;

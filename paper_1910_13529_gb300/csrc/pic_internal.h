@@ -91,6 +91,13 @@ struct CorrInst {
     float* J1;
 };
 
+// Current filter of one batched instance (all three components of J).
+struct FiltInst {
+    GridP g;
+    float* J;
+    int vec4;            // nz % 4 == 0 and J 16-byte aligned
+};
+
 // Device status word bits.
 enum : int { STATUS_CAPACITY = 1, STATUS_TIMEOUT = 2 };
 
@@ -126,6 +133,12 @@ cudaError_t launch_diag_reduce(const GridP& g, const StencilP& st, const float* 
                                cudaStream_t s);
 cudaError_t launch_kinetic(const GridP& g, const SpeciesP& sp, long long extent, double* acc,
                            cudaStream_t s);
+
+// ---- current filter along z (filter_kernels.cu) ----
+bool filter_vec4_ok(const float* J, int nz);
+cudaError_t launch_filter_current(const GridP& g, float* J, cudaStream_t s);
+cudaError_t launch_filter_rho(const GridP& g, double* rho, cudaStream_t s);
+cudaError_t launch_filter_current_batch(const FiltInst* inst, int ninst, long long max_rows3, cudaStream_t s);
 
 // ---- adjoint (adjoint_kernels.cu) ----
 cudaError_t launch_curl_plus_update(const GridP& g, const StencilP& st, const float* X, const float* Y, float a,

@@ -5,16 +5,16 @@ import ctypes
 import numpy as np
 import torch
 
-from . import (PIC_SOLVER_CUSTOM, PIC_SOLVER_YEE, encode_cells, pic_batch_create, pic_batch_destroy,
+from . import (PIC_FILTER_5PASS, PIC_FILTER_NONE, PIC_SOLVER_CUSTOM, PIC_SOLVER_YEE, encode_cells, pic_batch_create, pic_batch_destroy,
                pic_batch_instance, pic_batch_step, pic_bind_fields, pic_bind_species,
                pic_config, pic_create, pic_deposit, pic_destroy, pic_diag, pic_field_advance,
                pic_autotune, pic_gather_push, pic_gauss, pic_get_coefficients, pic_get_count, pic_get_state,
-               pic_get_tuning, pic_rho, pic_sort, pic_step, pic_sync)
+               pic_filter_current, pic_get_tuning, pic_rho, pic_sort, pic_step, pic_sync)
 
 
 def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee", M=16, coef=None,
                 fit_wk=0.0, fit_n=0.0, shape=1, moving_window=False, inject_species=-1,
-                inject_ppc=(1, 1, 1), rho_bg=0.0, sort_every=0):
+                inject_ppc=(1, 1, 1), rho_bg=0.0, sort_every=0, current_filter=False):
     c = pic_config()
     c.ndim, c.nz, c.nx, c.ny = int(ndim), int(nz), int(nx), int(ny if ndim == 3 else 1)
     c.dz, c.dx, c.dy, c.dt = float(dz), float(dx), float(dy), float(dt)
@@ -33,6 +33,7 @@ def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee"
         c.inject_ppc[i] = int(inject_ppc[i]) if i < len(inject_ppc) else 1
     c.rho_bg = float(rho_bg)
     c.sort_every = int(sort_every)
+    c.current_filter = PIC_FILTER_5PASS if current_filter else PIC_FILTER_NONE
     return c, keep
 
 
@@ -96,6 +97,10 @@ class Simulation:
 
     def sort(self):
         pic_sort(self.h, self.stream)
+
+    def filter_current(self):
+        """The 5-pass current filter along z, once, in place on J (pic_filter_current)."""
+        pic_filter_current(self.h, self.stream)
 
     def autotune(self):
         """Pick the fastest field-advance tile shape for this grid (pic_autotune)."""

@@ -20,7 +20,8 @@ def gpu_sim(grid, sps, coef=None, cap_extra=0, sort_every=0, ids=True):
               dx=grid["dx"], dy=grid.get("dy", grid["dx"]), dt=grid["dt"], shape=grid.get("shape", 1),
               solver=grid.get("solver", "yee"), moving_window=grid.get("moving_window", False),
               inject_species=grid.get("inject_species", -1), inject_ppc=grid.get("inject_ppc", (1, 1, 1)),
-              rho_bg=grid.get("rho_bg", 0.0), sort_every=sort_every)
+              rho_bg=grid.get("rho_bg", 0.0), sort_every=sort_every,
+              current_filter=grid.get("current_filter", False))
     if kw["solver"] == "custom":
         kw["coef"] = coef
     sim = Simulation(device="cuda:0", **kw)
@@ -44,7 +45,8 @@ def oracle_sim(grid, sps, coef=None):
         total = sum(len(sp["iz"]) for sp in sps[: grid["inject_species"] + 1])
         inject = dict(species=grid["inject_species"], ppc=grid["inject_ppc"],
                       next_id=max(len(sp["iz"]) for sp in sps))
-    return oc.Sim(g, species, h=h, moving_window=grid.get("moving_window", False), inject=inject)
+    return oc.Sim(g, species, h=h, moving_window=grid.get("moving_window", False), inject=inject,
+                  filt=grid.get("current_filter", False))
 
 
 def field_error(sim, osim):
