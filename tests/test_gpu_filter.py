@@ -34,8 +34,8 @@ def grid_of(ndim, nz, nx, ny, solver, shape, C=None, filt=True, d=(0.5, 0.4, 0.4
                 current_filter=filt)
 
 
-ROWS = [(2, 4, 3, 1), (2, 7, 5, 1), (2, 200, 24, 1), (2, 301, 9, 1), (2, 1024, 6, 1), (2, 2100, 5, 1),
-        (2, 5003, 3, 1), (3, 37, 6, 5), (3, 120, 12, 10)]
+ROWS = [(2, 4, 4, 1), (2, 7, 5, 1), (2, 200, 24, 1), (2, 301, 9, 1), (2, 1024, 6, 1), (2, 2100, 5, 1),
+        (2, 5003, 4, 1), (3, 37, 6, 5), (3, 120, 12, 10)]
 
 
 @pytest.mark.parametrize("nd,nz,nx,ny", ROWS)
