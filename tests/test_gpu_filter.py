@@ -186,7 +186,8 @@ def test_gauss_law_for_the_filtered_charge(nd, solver, shape, C):
     Gs = torch.full_like(G, float("nan"))
     P.pic_gauss_static(sim.h, Gs.data_ptr(), sim.stream)
     torch.cuda.synchronize()
-    assert torch.equal(Gs, G)
+    # (FP64 atomics in the charge deposit: equal up to the order of the additions)
+    assert (Gs - G).abs().max().item() <= 1e-12 * G.abs().max().item()
     d = sim.diag()
     margin = (len(C) + 24 + 2 if solver == "custom" else 2) + 5
     assert d["gauss_max"] == pytest.approx(G[..., margin:-margin].abs().max().item(), rel=1e-9, abs=1e-300)
