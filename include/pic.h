@@ -231,12 +231,12 @@ pic_status pic_sync(pic_t* h, void* stream);
 enum {
     PIC_T_PARTICLES = 0,   /* gather + push (+ deposit when fused), per species */
     PIC_T_DEPOSIT = 1,     /* unfused deposition and zeroing of J */
-    PIC_T_CORRECTION = 2,  /* Sec. 3 current correction */
+    PIC_T_CORRECTION = 2,  /* Sec. 3 current correction (without the filter) */
     PIC_T_FIELDS = 3,      /* field advance (and copies back to the bound arrays) */
     PIC_T_SORT = 4,        /* counting sort */
     PIC_T_WINDOW = 5,      /* injection of the new plasma column */
     PIC_T_DIAG = 6,        /* rho, Gauss residual, reductions */
-    PIC_T_FILTER = 7,      /* current filter along z */
+    PIC_T_FILTER = 7,      /* current filter along z (with the correction, one fused kernel) */
     PIC_TIMING_N = 8
 };
 pic_status pic_timing(pic_t* h, int enable);

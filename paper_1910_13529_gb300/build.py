@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpic.so")
 SOURCES = ["pic_api.cu", "field_kernels.cu", "particle_kernels.cu", "diag_kernels.cu", "adjoint_kernels.cu",
-           "filter_kernels.cu", "host_math.cpp"]
+           "current_kernels.cu", "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 

@@ -1,5 +1,5 @@
 // Field advance (Eq. 1 of Sec. 2.1, Yee operators of Sec. 2.2, customised axial stencil of
-// Sec. 3 / Appendix C) and the Sec. 3 current correction, for sm_103a.
+// Sec. 3 / Appendix C), for sm_103a.
 //
 // One kernel performs the whole leapfrog step out of place:
 //   B^{n+1/2} = B^n - dt/2 d+ x E^n
@@ -1272,63 +1272,6 @@ cudaError_t launch_fa_march_ring(const FieldP& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// In-place Sec. 3 correction J1[i] <- sum_{|m| <= hlen} h[m] J1[i - m] along z (J1 = 0 outside
-// 0 <= i < nz).  One CTA holds a whole z row in shared memory, so no other CTA reads the values
-// it overwrites.  Each thread produces four consecutive outputs from the (2 PIC_MAX_HLEN + 4)-float
-// window below them, read as aligned 128-bit shared loads (taps beyond hlen are zero).
-struct CorrP {
-    GridP g;
-    float h[2 * PIC_MAX_HLEN + 1];
-    int hlen;
-    float* J1;
-};
-
-__device__ __forceinline__ void correct_row(float* row, int nz, const float* __restrict__ h, float* s) {
-    constexpr int HL = PIC_MAX_HLEN;
-    constexpr int NWIN = 2 * HL + 4;               // window floats (a multiple of 4: HL even)
-    static_assert(NWIN % 4 == 0, "aligned windows");
-    const int nz4 = (nz + 3) & ~3;
-    // s[k] = J1[k - HL] for k < nz4 + 2 HL + 4 (zero outside the row)
-    for (int k = threadIdx.x; k < nz4 + NWIN; k += blockDim.x) {
-        const int gz = k - HL;
-        s[k] = (gz >= 0 && gz < nz) ? row[gz] : 0.f;
-    }
-    __syncthreads();
-    for (int i = 4 * threadIdx.x; i < nz; i += 4 * blockDim.x) {
-        float w[NWIN];
-#pragma unroll
-        for (int q = 0; q < NWIN / 4; ++q) {
-            const float4 v = *reinterpret_cast<const float4*>(s + i + 4 * q);
-            w[4 * q] = v.x;
-            w[4 * q + 1] = v.y;
-            w[4 * q + 2] = v.z;
-            w[4 * q + 3] = v.w;
-        }
-        // out[i + j] = sum_m h[m + HL] J1[i + j - m] = sum_k h[k] w[j + 2 HL - k]
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k <= 2 * HL; ++k)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[j] = fmaf(h[k], w[j + 2 * HL - k], acc[j]);
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-            if (i + j < nz) row[i + j] = acc[j];
-    }
-}
-
-__global__ void __launch_bounds__(256) correct_j1_kernel(CorrP p) {
-    extern __shared__ float4 s4[];
-    correct_row(p.J1 + (long long)blockIdx.x * p.g.nz, p.g.nz, p.h, reinterpret_cast<float*>(s4));
-}
-
-// Batched in-place correction: blockIdx.y = instance, blockIdx.x = z row of that instance.
-__global__ void __launch_bounds__(256) correct_j1_batch_kernel(const CorrInst* __restrict__ inst) {
-    extern __shared__ float4 s4[];
-    const CorrInst& q = inst[blockIdx.y];
-    if ((long long)blockIdx.x >= (long long)q.g.nx * q.g.ny) return;
-    correct_row(q.J1 + (long long)blockIdx.x * q.g.nz, q.g.nz, q.h, reinterpret_cast<float*>(s4));
-}
-
 template <int NDIM, int MAXM, int TZ, int TX, int TY>
 cudaError_t launch_fa_batch(const FieldP* inst, const int* tile_start, int ninst, int total, int parity,
                             cudaStream_t s) {
@@ -1366,18 +1309,6 @@ cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start
     if (maxm <= 4) return launch_fa_batch<3, 4, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
     if (maxm <= 8) return launch_fa_batch<3, 8, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
     return launch_fa_batch<3, 16, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
-}
-
-cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_rows, int max_nz, cudaStream_t s) {
-    if (ninst <= 0) return cudaSuccess;
-    size_t smem = sizeof(float) * (((max_nz + 3) & ~3) + 2 * PIC_MAX_HLEN + 4);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(correct_j1_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    correct_j1_batch_kernel<<<dim3((unsigned)max_rows, (unsigned)ninst), 256, smem, s>>>(inst);
-    return cudaGetLastError();
 }
 
 // Tile variants the autotuner chooses from.  2D: (TZ, TX); 3D: (TZ, TX, TY); rb = register-
@@ -1453,27 +1384,6 @@ cudaError_t launch_field_advance(const FieldP& p_in, cudaStream_t s, int variant
     if (M <= 4) return launch_fa_variant<3, 4>(p, variant, s);
     if (M <= 8) return launch_fa_variant<3, 8>(p, variant, s);
     return launch_fa_variant<3, 16>(p, variant, s);
-}
-
-cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s) {
-    CorrP p;
-    p.g = g;
-    p.hlen = hlen;
-    // taps centred on PIC_MAX_HLEN: p.h[PIC_MAX_HLEN + m] = h[m], zero for |m| > hlen
-    for (int i = 0; i < 2 * PIC_MAX_HLEN + 1; ++i) {
-        const int m = i - PIC_MAX_HLEN;
-        p.h[i] = (m >= -hlen && m <= hlen) ? taps[m + hlen] : 0.f;
-    }
-    p.J1 = J1;
-    size_t smem = sizeof(float) * (((g.nz + 3) & ~3) + 2 * PIC_MAX_HLEN + 4);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(correct_j1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    long long rows = (long long)g.nx * g.ny;
-    correct_j1_kernel<<<(unsigned)rows, 256, smem, s>>>(p);
-    return cudaGetLastError();
 }
 
 }  // namespace pic

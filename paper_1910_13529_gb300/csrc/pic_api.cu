@@ -220,6 +220,22 @@ pic_status advance_fields(pic_t* h, const float* Ein, const float* Bin, float* E
     return PIC_OK;
 }
 
+// After the deposit: the current filter on J1, J2, J3 and the Sec. 3 correction on J1, fused
+// into one launch when both are configured.
+pic_status smooth_current(pic_t* h, cudaStream_t s) {
+    if (h->cfg.current_filter && h->hlen > 0) {
+        Scope sc(h, PIC_T_FILTER, 1, s);
+        CK(h, launch_filter_correct(h->g, h->hf, h->hlen, h->J, s), "current filter + correction kernel");
+    } else if (h->cfg.current_filter) {
+        Scope sc(h, PIC_T_FILTER, 1, s);
+        CK(h, launch_filter_current(h->g, h->J, s), "current filter kernel");
+    } else if (h->hlen > 0) {
+        Scope sc(h, PIC_T_CORRECTION, 1, s);
+        CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
+    }
+    return PIC_OK;
+}
+
 pic_status ensure_sort_scratch(pic_t* h) {
     long long cap = 0;
     bool ids = false;
@@ -484,14 +500,7 @@ pic_status pic_deposit(pic_t* h, void* stream) {
         Scope sc(h, PIC_T_DEPOSIT, 1, s);
         CK(h, launch_deposit_unfused(h->g, sp, h->J, h->sp[i].extent, s), "deposit kernel");
     }
-    if (h->cfg.current_filter) {
-        Scope sc(h, PIC_T_FILTER, 1, s);
-        CK(h, launch_filter_current(h->g, h->J, s), "current filter kernel");
-    }
-    if (h->hlen > 0) {
-        Scope sc(h, PIC_T_CORRECTION, 1, s);
-        CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
-    }
+    if ((st = smooth_current(h, s))) return st;
     h->state = 2;
     return PIC_OK;
 }
@@ -534,14 +543,7 @@ pic_status pic_step(pic_t* h, int nsteps, void* stream) {
                "fused push/deposit kernel");
         }
         h->pending_shift = 0;
-        if (h->cfg.current_filter) {
-            Scope sc(h, PIC_T_FILTER, 1, s);
-            CK(h, launch_filter_current(h->g, h->J, s), "current filter kernel");
-        }
-        if (h->hlen > 0) {
-            Scope sc(h, PIC_T_CORRECTION, 1, s);
-            CK(h, launch_correct_j1(h->g, h->hf, h->hlen, h->J, s), "current correction kernel");
-        }
+        if ((st = smooth_current(h, s))) return st;
         if ((st = advance_fields(h, Ec, Bc, En, Bn, s))) return st;
         float* t = Ec;
         Ec = En;

@@ -105,7 +105,7 @@ enum : int { STATUS_CAPACITY = 1, STATUS_TIMEOUT = 2 };
 cudaError_t launch_field_advance(const FieldP& p, cudaStream_t s, int variant = 0);
 int field_variants(int ndim);
 int default_field_variant(int ndim, int M);
-cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s);
+
 // batched: instance tables live in device memory
 cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,
                                        int ndim, int maxm, int parity, cudaStream_t s);
@@ -134,7 +134,10 @@ cudaError_t launch_diag_reduce(const GridP& g, const StencilP& st, const float* 
 cudaError_t launch_kinetic(const GridP& g, const SpeciesP& sp, long long extent, double* acc,
                            cudaStream_t s);
 
-// ---- current filter along z (filter_kernels.cu) ----
+// ---- current filter and Sec. 3 correction along z (current_kernels.cu) ----
+cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s);
+// filter on J1, J2, J3 and the correction on J1 in one launch (J: the three components)
+cudaError_t launch_filter_correct(const GridP& g, const float* taps, int hlen, float* J, cudaStream_t s);
 bool filter_vec4_ok(const float* J, int nz);
 cudaError_t launch_filter_current(const GridP& g, float* J, cudaStream_t s);
 cudaError_t launch_filter_rho(const GridP& g, double* rho, cudaStream_t s);
