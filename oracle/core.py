@@ -50,18 +50,28 @@ def _d(a):
 
 
 class Grid:
-    """Grid, time step, axial stencil and particle shape of one oracle instance."""
+    """Grid, time step, axial stencil and particle shape of one oracle instance.
+
+    C: coefficients of the axial operators.  Cb (optional): separate coefficients of the
+    B-side operator d- ([k]_B1: Ampere's and Gauss's laws), C then being the E-side d+
+    ([k]_E1: Faraday's law); the shorter set is padded with zeros."""
 
     def __init__(self, ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, C=(1.0,), shape=1,
-                 periodic_z=False):
+                 periodic_z=False, Cb=None):
         self.ndim, self.nz, self.nx = int(ndim), int(nz), int(nx)
         self.ny = int(ny) if ndim == 3 else 1
         self.dz, self.dx, self.dy, self.dt = float(dz), float(dx), float(dy), float(dt)
-        self.C = np.ascontiguousarray(np.asarray(C, dtype=np.float64))
+        C = np.asarray(C, dtype=np.float64)
+        Cb = None if Cb is None else np.asarray(Cb, dtype=np.float64)
+        M = max(len(C), len(Cb) if Cb is not None else 0)
+        self.C = np.ascontiguousarray(np.pad(C, (0, M - len(C))))
+        self.Cb = None if Cb is None else np.ascontiguousarray(np.pad(Cb, (0, M - len(Cb))))
+        # what the C routines receive: C, followed by Cb when the operators are split
+        self.Cpar = self.C if self.Cb is None else np.ascontiguousarray(np.concatenate([self.C, self.Cb]))
         self.shape = int(shape)
         self.periodic_z = bool(periodic_z)
-        self.ip = (ctypes.c_int * 8)(self.ndim, self.nz, self.nx, self.ny, len(self.C), self.shape,
-                                     int(self.periodic_z), 0)
+        self.ip = (ctypes.c_int * 8)(self.ndim, self.nz, self.nx, self.ny, M, self.shape,
+                                     int(self.periodic_z), int(self.Cb is not None))
         self.dpar = (ctypes.c_double * 4)(self.dz, self.dx, self.dy, self.dt)
 
     @property
@@ -76,15 +86,15 @@ class Grid:
 
 
 def field_advance(g: Grid, E, B, J):
-    lib().or_field_advance(g.ip, g.dpar, _d(g.C), _d(E), _d(B), _d(J))
+    lib().or_field_advance(g.ip, g.dpar, _d(g.Cpar), _d(E), _d(B), _d(J))
 
 
 def faraday_half(g: Grid, E, B):
-    lib().or_faraday_half(g.ip, g.dpar, _d(g.C), _d(E), _d(B))
+    lib().or_faraday_half(g.ip, g.dpar, _d(g.Cpar), _d(E), _d(B))
 
 
 def ampere(g: Grid, E, B, J):
-    lib().or_ampere(g.ip, g.dpar, _d(g.C), _d(E), _d(B), _d(J))
+    lib().or_ampere(g.ip, g.dpar, _d(g.Cpar), _d(E), _d(B), _d(J))
 
 
 def correct_j1(g: Grid, h, J):
@@ -122,7 +132,7 @@ def rho(g: Grid, xi, Q, out=None):
 
 def gauss(g: Grid, E, rho_nodes):
     G = np.zeros(g.fshape[1:])
-    lib().or_gauss(g.ip, g.dpar, _d(g.C), _d(E), _d(np.ascontiguousarray(rho_nodes)), _d(G))
+    lib().or_gauss(g.ip, g.dpar, _d(g.Cpar), _d(E), _d(np.ascontiguousarray(rho_nodes)), _d(G))
     return G
 
 

@@ -81,15 +81,21 @@ def correction_kernel(C, hlen: int = 40, nfft: int = 8192) -> np.ndarray:
     return np.array([h[m % nfft] for m in range(-hlen, hlen + 1)])
 
 
-def cfl_dt(dz: float, dx_perp, C=None, nscan: int = 20001) -> float:
-    """Largest stable dt of the leapfrog: (dt/2)^2 (max [k]_1^2 + sum (2/dx_perp)^2) <= 1.
+def cfl_dt(dz: float, dx_perp, C=None, nscan: int = 20001, Cb=None) -> float:
+    """Largest stable dt of the leapfrog: (dt/2)^2 (max [k]_E1 [k]_B1 + sum (2/dx_perp)^2) <= 1.
 
-    Yee: C = None ([k]_1 max = 2/dz).  Customised: max over khat of the Appendix C symbol.
+    Yee: C = None ([k]_1 max = 2/dz).  Customised: max over khat of the Appendix C symbol
+    (squared), or of the product of the E-side (C) and B-side (Cb) symbols when they differ;
+    a product that changes sign has no stable dt (ValueError).
     """
     if C is None:
-        kmax = 2.0 / dz
+        kmax2 = (2.0 / dz) ** 2
     else:
         kh = np.linspace(0.0, math.pi / 2, nscan)
-        kmax = np.max(np.abs(axial_symbol(C, kh))) * 2.0 / dz
-    s = kmax ** 2 + sum((2.0 / d) ** 2 for d in dx_perp)
+        se = axial_symbol(C, kh)
+        prod = se * (se if Cb is None else axial_symbol(Cb, kh))
+        if prod.min() < -1e-12 * max(prod.max(), 1e-300):
+            raise ValueError("[k]_E1 [k]_B1 < 0 somewhere: unstable for every dt")
+        kmax2 = prod.max() * (2.0 / dz) ** 2
+    s = kmax2 + sum((2.0 / d) ** 2 for d in dx_perp)
     return 2.0 / math.sqrt(s)

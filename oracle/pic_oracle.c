@@ -40,6 +40,9 @@
  *   ip[0]=ndim ip[1]=nz ip[2]=nx ip[3]=ny ip[4]=M ip[5]=shape (1|2)
  *   ip[6]=periodic_z (0: zero outside z, the PIC runs; 1: periodic, for the
  *         plane-wave dispersion test only; honoured by the field operators)
+ *   ip[7]=split (0: one coefficient set C[0..M) for d+ and d-; 1: C[0..M) for the E-side
+ *         d+ ([k]_E1, Faraday's law) and C[M..2M) for the B-side d- ([k]_B1, Ampere's and
+ *         Gauss's laws): the "[k]_E1 != [k]_B1" option Sec. 3 mentions)
  *   dp[0]=dz dp[1]=dx dp[2]=dy dp[3]=dt
  */
 #include <math.h>
@@ -49,7 +52,8 @@
 typedef struct {
     int ndim, nz, nx, ny, M, shape, periodic_z;
     double dz, dx, dy, dt;
-    const double* C;
+    const double* C;    /* d+ (E side) */
+    const double* CB;   /* d- (B side) */
 } grid_t;
 
 static grid_t mk(const int* ip, const double* dp, const double* C) {
@@ -58,6 +62,7 @@ static grid_t mk(const int* ip, const double* dp, const double* C) {
     g.M = ip[4]; g.shape = ip[5]; g.periodic_z = ip[6];
     g.dz = dp[0]; g.dx = dp[1]; g.dy = dp[2]; g.dt = dp[3];
     g.C = C;
+    g.CB = (C && ip[7]) ? C + g.M : C;
     if (g.ndim == 2) g.ny = 1;
     return g;
 }
@@ -86,11 +91,11 @@ static double dzp(const grid_t* g, const double* f, int i, int j, int k) {
         s += g->C[l - 1] * (at(g, f, i + l, j, k) - at(g, f, i - l + 1, j, k));
     return s / g->dz;
 }
-/* Appendix C: d- f_i = sum_l C_l (f_{i+l-1} - f_{i-l}) / dz */
+/* Appendix C: d- f_i = sum_l C_l (f_{i+l-1} - f_{i-l}) / dz, with the B-side coefficients */
 static double dzm(const grid_t* g, const double* f, int i, int j, int k) {
     double s = 0.0;
     for (int l = 1; l <= g->M; ++l)
-        s += g->C[l - 1] * (at(g, f, i + l - 1, j, k) - at(g, f, i - l, j, k));
+        s += g->CB[l - 1] * (at(g, f, i + l - 1, j, k) - at(g, f, i - l, j, k));
     return s / g->dz;
 }
 /* transverse operators are always the two-point Yee differences (Sec. 2.2) */
