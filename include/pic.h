@@ -101,7 +101,8 @@ typedef struct pic_config {
     int solver;             /* PIC_SOLVER_YEE or PIC_SOLVER_CUSTOM */
     int M;                  /* customised: number of coefficients C_1..C_M, 1 <= M <= PIC_MAX_M */
     const double* coef;     /* customised: host array of M coefficients; NULL fits them
-                               (Appendix C, target [k1]_t = sin(k dt/2)/(dt/2), Sec. 3) */
+                               (Appendix C, target [k1]_t = sin(k dt/2)/(dt/2), Sec. 3).  They
+                               define d+ and d- alike ([k]_E1 = [k]_B1) unless coef_b is given */
     double fit_wk, fit_n;   /* fit weight exp(-ln2 (2k/w_k1)^n); 0 selects 0.6 and 10 */
     int shape;              /* 1: linear, 2: quadratic B-spline */
     int moving_window;      /* 1: the window moves one cell when n dt >= (s+1) dz */
@@ -110,13 +111,19 @@ typedef struct pic_config {
     double rho_bg;          /* uniform background charge density (Gauss diagnostic only) */
     int sort_every;         /* pic_step sorts particles by cell every sort_every steps (0: never) */
     int current_filter;     /* PIC_FILTER_NONE or PIC_FILTER_5PASS */
+    const double* coef_b;   /* NULL, or (customised solver with explicit coef) M coefficients of
+                               the B-side operator d- ([k]_B1: Ampere's and Gauss's laws and the
+                               Sec. 3 correction), coef then defining only the E-side d+ ([k]_E1,
+                               Faraday's law): the [k]_E1 != [k]_B1 solvers Sec. 3 allows, e.g.
+                               with [k]_E1 [k]_B1 = [k1]_t^2.  Not supported by pic_adjoint_step. */
 } pic_config;
 
 /* ---- handle ------------------------------------------------------------------------
  * pic_create validates cfg, fits the customised coefficients when cfg->coef is NULL,
- * computes the correction taps h, checks dt against the stability limit
- *   (dt/2)^2 (max_k [k]_1^2 + sum_perp (2/d_perp)^2) <= 1   (Sec. 2.1 leapfrog, App. C)
- * (PIC_ERR_CFL above it), and allocates the library's scratch on the current device:
+ * computes the correction taps h (from the B-side coefficients), checks dt against the
+ * stability limit
+ *   (dt/2)^2 (max_k [k]_E1 [k]_B1 + sum_perp (2/d_perp)^2) <= 1   (Eq. wave, leapfrog, App. C)
+ * (PIC_ERR_CFL above it; PIC_ERR_ARG if [k]_E1 [k]_B1 changes sign), and allocates the library's scratch on the current device:
  * the second field buffer of the out-of-place advance, the corrected-J1 buffer, sort and
  * diagnostic workspace.  Device memory: about 7 x 4 x nz nx ny bytes + 8 x nz nx ny.   */
 pic_status pic_create(const pic_config* cfg, pic_t** out);
@@ -133,8 +140,15 @@ pic_status pic_fit_coefficients(double kappa, int M, double wk, double n, double
 pic_status pic_correction_taps(const double* C, int M, int hlen, double* h_out);
 /* Largest stable dt for the given grid and axial stencil (M = 1, C = {1}: Yee).       */
 pic_status pic_cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M, double* dt_out);
-/* Coefficients and taps a handle uses (C_out: PIC_MAX_M, h_out: 2*PIC_MAX_HLEN+1). */
+/* The same for separate E-side (CE) and B-side (CB) coefficients, M each: the limit of the
+ * product [k]_E1 [k]_B1; PIC_ERR_ARG if that product changes sign (no stable dt).         */
+pic_status pic_cfl_dt_split(int ndim, double dz, double dx, double dy, const double* CE, const double* CB, int M,
+                            double* dt_out);
+/* Coefficients and taps a handle uses (C_out: PIC_MAX_M, h_out: 2*PIC_MAX_HLEN+1); C_out is
+ * the E-side set.  pic_get_coefficients_b: the B-side set (Cb_out: PIC_MAX_M) and whether it
+ * was given separately (split = 1).                                                     */
 pic_status pic_get_coefficients(const pic_t* h, double* C_out, int* M, double* h_out, int* hlen);
+pic_status pic_get_coefficients_b(const pic_t* h, double* Cb_out, int* split);
 
 /* ---- binding caller-owned device memory ---------------------------------------------
  * E, B, J: device pointers to 3 * ny * nx * nz floats each (layout above).  The library
@@ -247,7 +261,7 @@ pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream
  * fields (a rigidly moving beam), pic_adjoint_step takes the adjoint (aE, aB) = dL/d(E, B) at
  * the end of one step back to the start of that step and adds the step's contribution to
  * dL/dC_l (the Sec. 3 / Appendix C axial coefficients, including their effect through the
- * Sec. 3 current correction) to grad.
+ * Sec. 3 current correction) to grad.  Handles created with coef_b are refused (PIC_ERR_ARG).
  *   E, B:   forward fields at the start of the step (device, 3 nz nx ny floats each);
  *   J:      the (filtered and corrected) current of that step, as pic_step / pic_deposit left
  *           it in J (the filter precedes the correction and does not depend on C);

@@ -25,7 +25,7 @@ DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "co
 
 # exported symbols declared in include/pic.h
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_correction_taps",
-           "pic_cfl_dt", "pic_get_coefficients", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
+           "pic_cfl_dt", "pic_cfl_dt_split", "pic_get_coefficients", "pic_get_coefficients_b", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
            "pic_deposit", "pic_field_advance", "pic_step", "pic_filter_current", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
            "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
            "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy",
@@ -48,6 +48,7 @@ class pic_config(ctypes.Structure):
         ("fit_wk", ctypes.c_double), ("fit_n", ctypes.c_double), ("shape", ctypes.c_int),
         ("moving_window", ctypes.c_int), ("inject_species", ctypes.c_int), ("inject_ppc", ctypes.c_int * 3),
         ("rho_bg", ctypes.c_double), ("sort_every", ctypes.c_int), ("current_filter", ctypes.c_int),
+        ("coef_b", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -66,6 +67,9 @@ def _load():
         "pic_cfl_dt": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int, dp],
                        ctypes.c_int),
         "pic_get_coefficients": ([vp, dp, ip, dp, ip], ctypes.c_int),
+        "pic_get_coefficients_b": ([vp, dp, ip], ctypes.c_int),
+        "pic_cfl_dt_split": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
+                              ctypes.c_int, dp], ctypes.c_int),
         "pic_bind_fields": ([vp, vp, vp, vp], ctypes.c_int),
         "pic_bind_species": ([vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double], ctypes.c_int),
@@ -160,6 +164,23 @@ def pic_cfl_dt(ndim, dz, dx, dy, C):
     out = ctypes.c_double()
     _check(lib.pic_cfl_dt(int(ndim), float(dz), float(dx), float(dy), _dptr(C), len(C), ctypes.byref(out)))
     return out.value
+
+
+def pic_cfl_dt_split(ndim, dz, dx, dy, CE, CB):
+    M = max(len(CE), len(CB))
+    CE = np.ascontiguousarray(np.pad(np.asarray(CE, dtype=np.float64), (0, M - len(CE))))
+    CB = np.ascontiguousarray(np.pad(np.asarray(CB, dtype=np.float64), (0, M - len(CB))))
+    out = ctypes.c_double()
+    _check(lib.pic_cfl_dt_split(int(ndim), float(dz), float(dx), float(dy), _dptr(CE), _dptr(CB), M,
+                                ctypes.byref(out)))
+    return out.value
+
+
+def pic_get_coefficients_b(h):
+    Cb = np.zeros(PIC_MAX_M)
+    split = ctypes.c_int()
+    _check(lib.pic_get_coefficients_b(h, _dptr(Cb), ctypes.byref(split)), h)
+    return Cb, bool(split.value)
 
 
 def pic_get_coefficients(h):

@@ -20,7 +20,7 @@ __device__ double div_e(const GridP& g, const StencilP& st, const float* E, int 
         int a = i + l - 1, b = i - l;
         double fa = (a >= 0 && a < g.nz) ? ld(E, row + a) : 0.0;
         double fb = (b >= 0 && b < g.nz) ? ld(E, row + b) : 0.0;
-        dz += (double)st.C[l - 1] * (fa - fb);
+        dz += (double)st.Cm[l - 1] * (fa - fb);   // the B-side d- of Ampere's law
     }
     dz /= (double)g.dz;
     int jm = j == 0 ? g.nx - 1 : j - 1;

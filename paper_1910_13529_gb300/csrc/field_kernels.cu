@@ -66,12 +66,11 @@ __device__ __forceinline__ void advance_tile(const FieldP& p, int tz, int tx, in
     const float dt = g.dt;
     const float hx = 0.5f * dt / g.dx, fx = dt / g.dx;
     const float hy = NDIM == 3 ? 0.5f * dt / g.dy : 0.f, fy = NDIM == 3 ? dt / g.dy : 0.f;
-    float Ch[MAXM], Cf[MAXM];
+    float Ch[MAXM], Cf[MAXM];      // d+ of the half B steps (E side), d- of the E step (B side)
 #pragma unroll
     for (int l = 0; l < MAXM; ++l) {
-        float c = l < M ? p.st.C[l] : 0.f;
-        Ch[l] = c * (0.5f * dt / g.dz);
-        Cf[l] = c * (dt / g.dz);
+        Ch[l] = (l < M ? p.st.C[l] : 0.f) * (0.5f * dt / g.dz);
+        Cf[l] = (l < M ? p.st.Cm[l] : 0.f) * (dt / g.dz);
     }
 
     // ---- stage 0: E^n over the full halo -------------------------------------------
@@ -317,8 +316,8 @@ __device__ __forceinline__ void stage_rows(float* dst, int cstride, const float*
 }
 
 // w[k] = f[z - MP + k], k < 2 MP + 4, from the aligned window at s.
-//   d+ (E -> B, Appendix C):  d[j] = sum_l C_l (f[z+j+l] - f[z+j-l+1]),  l = 1..M
-//   d- (B -> E):              d[j] = sum_l C_l (f[z+j+l-1] - f[z+j-l])
+//   d+ (E -> B, Appendix C):  d[j] = sum_l C_l (f[z+j+l] - f[z+j-l+1]),  l = 1..M  (E-side C)
+//   d- (B -> E):              d[j] = sum_l C_l (f[z+j+l-1] - f[z+j-l])          (B-side Cm)
 // mid[j] = f[z+j].  Coefficients beyond M are zero.
 template <int MAXM, int MP, bool PLUS>
 __device__ __forceinline__ void window_dz(const StencilP& st, const float* s, float (&d)[4], float (&mid)[4]) {
@@ -339,7 +338,7 @@ __device__ __forceinline__ void window_dz(const StencilP& st, const float* s, fl
 #pragma unroll
         for (int l = 1; l <= MAXM; ++l) {
             const float df = PLUS ? w[MP + j + l] - w[MP + j - l + 1] : w[MP + j + l - 1] - w[MP + j - l];
-            acc = fmaf(st.C[l - 1], df, acc);
+            acc = fmaf(PLUS ? st.C[l - 1] : st.Cm[l - 1], df, acc);
         }
         d[j] = acc;
         mid[j] = w[MP + j];

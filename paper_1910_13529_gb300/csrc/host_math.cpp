@@ -137,20 +137,29 @@ int correction_taps(const double* C, int M, int hlen, double* h) {
     return 0;
 }
 
-// Leapfrog limit (dt/2)^2 (max [k]_1^2 + sum (2/d_perp)^2) <= 1.
-double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M) {
-    double kmax = 0.0;
+// Leapfrog limit (dt/2)^2 (max [k]_E1 [k]_B1 + sum (2/d_perp)^2) <= 1 (Eq. wave); [k]_E1 = [k]_B1
+// for the symmetric stencils.
+double cfl_dt_split(int ndim, double dz, double dx, double dy, const double* CE, const double* CB, int M) {
+    double pmax = 0.0, pmin = 0.0;
     const int ns = 20001;
     for (int q = 0; q < ns; ++q) {
         double t = 0.5 * M_PI * q / (ns - 1);
-        double s = 0.0;
-        for (int l = 0; l < M; ++l) s += C[l] * std::sin((2 * l + 1) * t);
-        kmax = std::fmax(kmax, std::fabs(s));
+        double se = 0.0, sb = 0.0;
+        for (int l = 0; l < M; ++l) {
+            se += CE[l] * std::sin((2 * l + 1) * t);
+            sb += CB[l] * std::sin((2 * l + 1) * t);
+        }
+        pmax = std::fmax(pmax, se * sb);
+        pmin = std::fmin(pmin, se * sb);
     }
-    kmax *= 2.0 / dz;
-    double s = kmax * kmax + (2.0 / dx) * (2.0 / dx);
+    if (pmin < -1e-12 * std::fmax(pmax, 1e-300)) return -1.0;
+    double s = pmax * (2.0 / dz) * (2.0 / dz) + (2.0 / dx) * (2.0 / dx);
     if (ndim == 3) s += (2.0 / dy) * (2.0 / dy);
     return 2.0 / std::sqrt(s);
+}
+
+double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M) {
+    return cfl_dt_split(ndim, dz, dx, dy, C, C, M);
 }
 
 }  // namespace pic

@@ -31,7 +31,9 @@ struct pic_t {
     pic_config cfg;
     GridP g;
     StencilP st;
-    double C64[PIC_MAX_M];
+    double C64[PIC_MAX_M];        // E-side d+ coefficients
+    double C64b[PIC_MAX_M];       // B-side d- coefficients (= C64 unless split)
+    bool split = false;
     double h64[2 * PIC_MAX_HLEN + 1];
     float hf[2 * PIC_MAX_HLEN + 1];
     int hlen = 0;
@@ -300,6 +302,17 @@ pic_status pic_correction_taps(const double* C, int M, int hlen, double* h_out) 
     return correction_taps(C, M, hlen, h_out) ? PIC_ERR_ARG : PIC_OK;
 }
 
+pic_status pic_cfl_dt_split(int ndim, double dz, double dx, double dy, const double* CE, const double* CB, int M,
+                            double* dt_out) {
+    if (!dt_out || !CE || !CB || M < 1 || M > PIC_MAX_M || (ndim != 2 && ndim != 3) || !(dz > 0) || !(dx > 0) ||
+        (ndim == 3 && !(dy > 0)))
+        return PIC_ERR_ARG;
+    const double dt = cfl_dt_split(ndim, dz, dx, dy, CE, CB, M);
+    if (dt < 0.0) return PIC_ERR_ARG;
+    *dt_out = dt;
+    return PIC_OK;
+}
+
 pic_status pic_cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M, double* dt_out) {
     if (!dt_out || !C || M < 1 || M > PIC_MAX_M || (ndim != 2 && ndim != 3) || !(dz > 0) || !(dx > 0) ||
         (ndim == 3 && !(dy > 0)))
@@ -331,6 +344,9 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
         return fail(nullptr, PIC_ERR_ARG, "inject_ppc must be >= 1");
     int M = 1;
     double C[PIC_MAX_M] = {1.0};
+    double CB[PIC_MAX_M] = {1.0};
+    if (c.coef_b && (c.solver != PIC_SOLVER_CUSTOM || !c.coef))
+        return fail(nullptr, PIC_ERR_ARG, "coef_b needs the customised solver with explicit coef");
     if (c.solver == PIC_SOLVER_CUSTOM) {
         M = c.M;
         if (M < 1 || M > PIC_MAX_M) return fail(nullptr, PIC_ERR_ARG, "M must be in [1, %d]", PIC_MAX_M);
@@ -339,8 +355,11 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
         } else if (fit_coefficients(c.dz / c.dt, M, c.fit_wk, c.fit_n, C)) {
             return fail(nullptr, PIC_ERR_ARG, "coefficient fit failed");
         }
+        for (int l = 0; l < M; ++l) CB[l] = c.coef_b ? c.coef_b[l] : C[l];
     }
-    double dtmax = cfl_dt(c.ndim, c.dz, c.dx, c.dy, C, M);
+    const bool split = c.coef_b != nullptr;
+    double dtmax = cfl_dt_split(c.ndim, c.dz, c.dx, c.dy, C, CB, M);
+    if (dtmax < 0.0) return fail(nullptr, PIC_ERR_ARG, "[k]_E1 [k]_B1 changes sign: unstable for every dt");
     if (c.dt > dtmax * (1.0 + 1e-12))
         return fail(nullptr, PIC_ERR_CFL, "dt = %.6g above the stability limit %.6g", c.dt, dtmax);
 
@@ -349,6 +368,8 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     h->cfg = c;
     h->cfg.ny = ny;
     h->cfg.coef = nullptr;
+    h->cfg.coef_b = nullptr;
+    h->split = split;
     if (c.ndim == 2) h->cfg.dy = 1.0;
     cudaGetDevice(&h->device);
     GridP& g = h->g;
@@ -365,13 +386,18 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     g.shape = c.shape;
     h->st.M = M;
     h->fa_variant = default_field_variant(c.ndim, M);
+    bool yee_b = true;     // B-side d- is the two-point Yee difference: no correction
     for (int l = 0; l < PIC_MAX_M; ++l) {
         h->C64[l] = l < M ? C[l] : 0.0;
+        h->C64b[l] = l < M ? CB[l] : 0.0;
         h->st.C[l] = (float)h->C64[l];
+        h->st.Cm[l] = (float)h->C64b[l];
+        yee_b = yee_b && h->C64b[l] == (l == 0 ? 1.0 : 0.0);
     }
-    if (c.solver == PIC_SOLVER_CUSTOM && M > 1) {
+    // Sec. 3 correction: P = [k]_B1 / [k]_Yee, from the B-side coefficients
+    if (c.solver == PIC_SOLVER_CUSTOM && (split ? !yee_b : M > 1)) {
         h->hlen = PIC_MAX_HLEN;
-        if (correction_taps(C, M, h->hlen, h->h64)) {
+        if (correction_taps(CB, M, h->hlen, h->h64)) {
             delete h;
             return fail(nullptr, PIC_ERR_ARG, "stencil symbol ratio has a zero: no current correction");
         }
@@ -412,6 +438,14 @@ pic_status pic_destroy(pic_t* h) {
         dfree(q.prev_off);
     }
     delete h;
+    return PIC_OK;
+}
+
+pic_status pic_get_coefficients_b(const pic_t* h, double* Cb_out, int* split) {
+    if (!h) return PIC_ERR_ARG;
+    if (Cb_out)
+        for (int l = 0; l < PIC_MAX_M; ++l) Cb_out[l] = h->C64b[l];
+    if (split) *split = h->split ? 1 : 0;
     return PIC_OK;
 }
 
@@ -738,6 +772,7 @@ pic_status pic_timing_read(pic_t* h, double* ms, int64_t* launches, void* stream
 pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const float* J, float* aE, float* aB,
                             double* grad, void* stream) {
     if (!h || !E || !B || !J || !aE || !aB || !grad) return PIC_ERR_ARG;
+    if (h->split) return fail(h, PIC_ERR_ARG, "pic_adjoint_step needs one coefficient set (no coef_b)");
     const long long N = h->g.ncell;
     if (!h->adj_scratch) {
         pic_status st = dalloc(h, &h->adj_scratch, 7 * N, "adjoint scratch");

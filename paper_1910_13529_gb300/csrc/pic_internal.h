@@ -36,10 +36,13 @@ struct GridP {
     FastDiv div_nzg, div_nx;   // filled by the particle launchers
 };
 
-// Axial stencil (Appendix C).  M = 1, C[0] = 1 is the Yee difference.
+// Axial stencil (Appendix C).  M = 1, C[0] = 1 is the Yee difference.  C: the E-side d+
+// (Faraday's law, [k]_E1); Cm: the B-side d- (Ampere's and Gauss's laws, [k]_B1), equal to C
+// unless the handle was created with separate B-side coefficients.
 struct StencilP {
     int M;
     float C[PIC_MAX_M];
+    float Cm[PIC_MAX_M];
 };
 
 // Field-advance launch parameters.
@@ -159,5 +162,7 @@ cudaError_t launch_grad_corr(const GridP& g, int M, const float* W, const float*
 int fit_coefficients(double kappa, int M, double wk, double n, double* C);
 int correction_taps(const double* C, int M, int hlen, double* h);
 double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M);
+// with the E-side (CE) and B-side (CB) symbols: max of their product; -1 if the product is negative
+double cfl_dt_split(int ndim, double dz, double dx, double dy, const double* CE, const double* CB, int M);
 
 }  // namespace pic

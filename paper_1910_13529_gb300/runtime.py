@@ -14,7 +14,7 @@ from . import (PIC_FILTER_5PASS, PIC_FILTER_NONE, PIC_SOLVER_CUSTOM, PIC_SOLVER_
 
 def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee", M=16, coef=None,
                 fit_wk=0.0, fit_n=0.0, shape=1, moving_window=False, inject_species=-1,
-                inject_ppc=(1, 1, 1), rho_bg=0.0, sort_every=0, current_filter=False):
+                inject_ppc=(1, 1, 1), rho_bg=0.0, sort_every=0, current_filter=False, coef_b=None):
     c = pic_config()
     c.ndim, c.nz, c.nx, c.ny = int(ndim), int(nz), int(nx), int(ny if ndim == 3 else 1)
     c.dz, c.dx, c.dy, c.dt = float(dz), float(dx), float(dy), float(dt)
@@ -34,6 +34,21 @@ def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee"
     c.rho_bg = float(rho_bg)
     c.sort_every = int(sort_every)
     c.current_filter = PIC_FILTER_5PASS if current_filter else PIC_FILTER_NONE
+    if coef_b is not None:
+        # the E-side and B-side sets share M: pad the shorter one with zeros (without coef the
+        # library refuses coef_b)
+        cb_in = np.asarray(coef_b, dtype=np.float64)
+        M = max(len(keep) if keep is not None else 0, len(cb_in))
+        cb = np.zeros(M)
+        cb[: len(cb_in)] = cb_in
+        ce = None
+        if keep is not None:
+            ce = np.zeros(M)
+            ce[: len(keep)] = keep
+            c.coef = ce.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.coef_b = cb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c.M = M
+        keep = (ce, cb)
     return c, keep
 
 

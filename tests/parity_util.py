@@ -24,6 +24,8 @@ def gpu_sim(grid, sps, coef=None, cap_extra=0, sort_every=0, ids=True):
               current_filter=grid.get("current_filter", False))
     if kw["solver"] == "custom":
         kw["coef"] = coef
+        if grid.get("coef_b") is not None:
+            kw["coef_b"] = grid["coef_b"]
     sim = Simulation(device="cuda:0", **kw)
     for s, sp in enumerate(sps):
         n = len(sp["iz"])
@@ -35,9 +37,13 @@ def gpu_sim(grid, sps, coef=None, cap_extra=0, sort_every=0, ids=True):
 def oracle_sim(grid, sps, coef=None):
     nd = grid["ndim"]
     C = (1.0,) if grid.get("solver", "yee") == "yee" else coef
+    Cb = grid.get("coef_b") if grid.get("solver", "yee") == "custom" else None
     g = oc.Grid(nd, grid["nz"], grid["nx"], grid.get("ny", 1), grid["dz"], grid["dx"],
-                grid.get("dy", grid["dx"]), grid["dt"], C=C, shape=grid.get("shape", 1))
-    h = None if grid.get("solver", "yee") == "yee" else fit.correction_kernel(C, hlen=40)
+                grid.get("dy", grid["dx"]), grid["dt"], C=C, shape=grid.get("shape", 1), Cb=Cb)
+    # Sec. 3 correction from the B-side coefficients (none when the B side is the Yee difference)
+    CBeff = C if Cb is None else Cb
+    yee_b = Cb is not None and np.allclose(np.asarray(Cb, dtype=np.float64), np.eye(1, len(Cb))[0], rtol=0, atol=0)
+    h = None if grid.get("solver", "yee") == "yee" or yee_b else fit.correction_kernel(CBeff, hlen=40)
     species = [oc.Species(wl.xi_of(sp, nd), sp["u"].T.astype(np.float64), sp["q"], sp["m"], sp["w"],
                           ids=sp["ids"]) for sp in sps]
     inject = None

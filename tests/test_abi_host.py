@@ -63,6 +63,21 @@ def test_taps_and_cfl_match_oracle(P):
     assert P.pic_cfl_dt(2, 0.05, 0.05, 0.05, [1.0]) == pytest.approx(0.05 / np.sqrt(2), rel=1e-14)
 
 
+def test_split_cfl_matches_oracle(P):
+    """[k]_E1 != [k]_B1 (Sec. 3): the limit of the product of the two axial symbols."""
+    from oracle import fit
+    CE, CB = [1.0], fit.fit_coefficients(3.0, M=8)
+    for nd, d in [(2, (0.02, 0.02, 0.02)), (3, (0.02, 0.05, 0.05))]:
+        a = P.pic_cfl_dt_split(nd, *d, CE, CB)
+        b = fit.cfl_dt(d[0], list(d[1:nd]), CE, Cb=CB)
+        assert a == pytest.approx(b, rel=1e-9)
+    # identical sets give the symmetric limit; a sign-changing product has none
+    assert P.pic_cfl_dt_split(2, 0.05, 0.05, 0.05, CB, CB) == pytest.approx(P.pic_cfl_dt(2, 0.05, 0.05, 0.05, CB),
+                                                                           rel=1e-14)
+    with pytest.raises(P.PicError):
+        P.pic_cfl_dt_split(2, 0.05, 0.05, 0.05, [1.0], [-1.0])
+
+
 def _cfg(P, **kw):
     from paper_1910_13529_gb300.runtime import make_config
     base = dict(ndim=2, nz=64, nx=32, dz=0.05, dx=0.05, dt=0.02, shape=1)
