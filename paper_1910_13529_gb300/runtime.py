@@ -230,6 +230,8 @@ class StencilLoss:
     """Field energy left behind a rigidly moving beam after `nsteps`, as a function of the axial
     stencil coefficients C, with its gradient from the hand-written adjoint (pic_adjoint_step).
 
+    With grid["current_filter"] the 5-pass current filter runs in every step; it precedes the
+    correction and does not depend on C, so the adjoint step is unchanged.
     The particles are held rigid (their momenta never change) by giving them an effectively
     infinite mass; the loss is (1/2) sum (E^2 + B^2) dV over the cells with z index below
     (beam z index - behind).  The forward pass keeps a checkpoint (fields and particles) every
@@ -245,7 +247,8 @@ class StencilLoss:
         self.device = torch.device(device)
 
     def _sim(self, C):
-        kw = {k: self.grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape") if k in self.grid}
+        kw = {k: self.grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape", "current_filter")
+              if k in self.grid}
         sim = Simulation(device=str(self.device), solver="custom", coef=np.asarray(C, dtype=np.float64), **kw)
         for s, sp in enumerate(self.species):
             sim.add_species(s, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], self.RIGID_MASS, sp["w"])

@@ -126,6 +126,15 @@ def test_batch_with_split_and_symmetric_instances():
     batch.close()
 
 
+def test_symmetric_handles_report_one_set():
+    sim = gpu_sim(dict(ndim=2, nz=64, nx=8, ny=1, dz=0.5, dx=0.4, dy=0.4, dt=0.05, solver="custom", shape=1),
+                  [], coef=FIT8)
+    Cb, split = P.pic_get_coefficients_b(sim.h)
+    C, _ = P.pic_get_coefficients(sim.h)
+    assert not split and np.array_equal(Cb[: len(C)], C)
+    sim.close()
+
+
 def test_refusals():
     grid, CE = grid_of(2, 64, 8, 1, "yeeE-fitB")
     sim = gpu_sim(grid, [], coef=CE)
