@@ -93,6 +93,8 @@ enum {
     PIC_DIAG_INTERIOR = 9     /* number of nodes in the residual */
 };
 
+/* Zero-initialise a pic_config (memset or "= {0}") before setting fields: every option
+ * defaults to off at 0 / NULL (current_filter, coef_b, ...).                               */
 typedef struct pic_config {
     int ndim;               /* 2: (z, x); 3: (z, x, y) */
     int nz, nx, ny;         /* cells along z, x, y (ny ignored in 2D); nz, nx >= 2 */

@@ -74,6 +74,31 @@ def test_filtered_self_forces_table2():
     check("custom_F1_quadratic_5pass", kspace.self_force_custom(4.0, 1.0, 2, printed=True, filt=True))
 
 
+MUTATED_FILTERS = {
+    "flat compensator (-1, 3, -1)": ((0.25, 0.5),) * 4 + ((-1.0, 3.0),),
+    "no compensator": ((0.25, 0.5),) * 4,
+    "three binomial passes + compensator": ((0.25, 0.5),) * 3 + ((-1.25, 3.5),),
+    "five binomial passes + compensator": ((0.25, 0.5),) * 5 + ((-1.25, 3.5),),
+    "compensator first, then four passes (same product)": None,
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATED_FILTERS))
+def test_table2_pins_reject_other_filters(name, monkeypatch):
+    """The Table 2 pins discriminate: every other plausible filter misses at least one printed
+    value (the pass order alone cannot matter, the symbol being a product)."""
+    passes = MUTATED_FILTERS[name]
+    if passes is None:
+        passes = ((-1.25, 3.5),) + ((0.25, 0.5),) * 4
+    monkeypatch.setattr(kspace, "FILTER_PASSES", passes)
+    got = [sig(kspace.self_force_yee(4.0, 1.0, 2, filt=True), 2),
+           sig(kspace.self_force_spectral(4.0, 1.0, 2, filt=True), 2),
+           sig(kspace.self_force_custom(4.0, 1.0, 2, printed=True, filt=True), 2)]
+    want = [P[n][0] for n in ("yee_F1_quadratic_5pass", "spectral_F1_quadratic_5pass", "custom_F1_quadratic_5pass")]
+    same = all(g == pytest.approx(w, abs=1e-12) for g, w in zip(got, want))
+    assert same == ("same product" in name), (name, got)
+
+
 def test_filter_symbol_limits():
     # DC passes unchanged, the grid Nyquist mode (khat = pi/2) is removed, the symbol stays in [0, 1.1]
     assert kspace.filter_symbol(0.0) == pytest.approx(1.0, abs=1e-15)
