@@ -103,6 +103,34 @@ def test_deposit_with_filter(name, nd, solver, shape, C):
     sim.close()
 
 
+@pytest.mark.parametrize("nz", [1000, 2048, 3001, 4100])
+def test_fused_filter_and_correction_on_long_rows(nz):
+    """The fused kernel at every CTA size it takes (128 threads up to nz = 1024, 256 beyond) and over
+    several segments per row (nz > 2048), with and without 16-byte rows (nz % 4)."""
+    grid = grid_of(2, nz, 4, 1, "custom", 2, C=TABLE1)
+    sp = wl.random_particles(2, nz, 4, 1, 4000, seed=nz, u_scale=1.5, u_drift=(2.0, 0.3, -0.2), margin=6)
+    sim = gpu_sim(grid, [sp], coef=TABLE1)
+    osim = oracle_sim(grid, [sp], coef=TABLE1)
+    P.pic_timing(sim.h, 1)
+    sim.gather_push()
+    sim.deposit()
+    _, launches = P.pic_timing_read(sim.h, sim.stream)
+    P.pic_timing(sim.h, 0)
+    assert launches["filter"] == 1 and launches["correction"] == 0
+    g = osim.g
+    s = osim.species[0]
+    eb = oc.gather(g, osim.E, osim.B, s.xi)
+    oc.boris(eb, s.u, s.q * g.dt / (2 * s.m))
+    xi1 = oc.move(g, s.xi, s.u)
+    J = g.zeros()
+    oc.deposit(g, s.xi, xi1, s.u, s.Q, J)
+    oc.filter_z(g, J)
+    oc.correct_j1(g, osim.h, J)
+    Jg = sim.J.double().cpu().numpy()
+    assert np.abs(Jg - J).max() < TOL * np.abs(J).max()
+    sim.close()
+
+
 @pytest.mark.parametrize("name,nd,solver,shape,C", DEPOSIT_CASES)
 def test_steps_with_filter(name, nd, solver, shape, C):
     nz, nx, ny = (261, 20, 1) if nd == 2 else (100, 10, 9)
