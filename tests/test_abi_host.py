@@ -98,6 +98,40 @@ def test_bad_configs_are_refused_on_host(P, kw, status):
     assert len(P.pic_last_error()) > 0
 
 
+def test_new_options_are_validated_on_host(P):
+    from oracle import fit
+    F8 = fit.fit_coefficients(3.0, M=8)
+    c, keep = _cfg(P)
+    c.current_filter = 7
+    with pytest.raises(P.PicError) as ei:
+        P.pic_create(c)
+    assert ei.value.status == P.PIC_ERR_ARG and "current_filter" in P.pic_last_error()
+    bad = [
+        (dict(solver="custom", coef_b=F8), P.PIC_ERR_ARG),                  # no explicit E-side set
+        (dict(solver="yee", coef_b=F8), P.PIC_ERR_ARG),                     # split needs the customised solver
+        (dict(solver="custom", coef=[1.0], coef_b=[-1.0]), P.PIC_ERR_ARG),  # product changes sign
+        (dict(solver="custom", coef=[1.0], coef_b=F8, dt=0.05), P.PIC_ERR_CFL),
+    ]
+    for kw, status in bad:
+        c, keep = _cfg(P, **kw)
+        with pytest.raises(P.PicError) as ei:
+            P.pic_create(c)
+        assert ei.value.status == status, kw
+
+
+def test_make_config_pads_the_two_coefficient_sets(P):
+    c, keep = _cfg(P, solver="custom", coef=[1.0], coef_b=[0.9, 0.05, -0.01])
+    assert c.M == 3
+    ce, cb = keep
+    assert list(ce) == [1.0, 0.0, 0.0] and list(cb) == [0.9, 0.05, -0.01]
+    assert [c.coef[i] for i in range(3)] == [1.0, 0.0, 0.0]
+    assert [c.coef_b[i] for i in range(3)] == [0.9, 0.05, -0.01]
+    c, keep = _cfg(P, solver="custom", coef=[1.1, -0.05, 0.01, 0.002], coef_b=[1.0])
+    assert c.M == 4 and [c.coef_b[i] for i in range(4)] == [1.0, 0.0, 0.0, 0.0]
+    c, keep = _cfg(P)
+    assert not c.coef_b and c.current_filter == P.PIC_FILTER_NONE
+
+
 def test_null_handle_calls_return_arg_error(P):
     assert P.lib.pic_step(None, 1, None) == P.PIC_ERR_ARG
     assert P.lib.pic_diag(None, None, None) == P.PIC_ERR_ARG
