@@ -19,5 +19,7 @@ Pins (tests/test_oracle_*.py): plane-wave dispersion of Eq. wave, Gauss's law ke
 to round-off, Esirkepov continuity, Boris closed forms, dense-matrix brute force on
 8x8 grids, Table 1 re-fit, the self-force and kappa_r values of Sec. 2-3.
 The 5-pass current filter (named, not defined, in the paper) is pinned through its k-space
-symbol to the three filtered self-forces of Table 2.
+symbol to the three filtered self-forces of Table 2.  The split axial operators ([k]_E1 != [k]_B1,
+Sec. 3) are pinned by the dispersion relation with the product of the two symbols, each side's
+operator, div curl = 0 and Gauss's law with the B-side correction (tests/test_oracle_split.py).
 """
