@@ -16,8 +16,11 @@ Modules:
                 filter), kappa_r, on-axis E1, Appendix D closed forms
 
 Pins (tests/test_oracle_*.py): plane-wave dispersion of Eq. wave, Gauss's law kept
-to round-off, Esirkepov continuity, Boris closed forms, dense-matrix brute force on
-8x8 grids, Table 1 re-fit, the self-force and kappa_r values of Sec. 2-3.
+to round-off, Esirkepov continuity, Boris closed forms, the position update against
+relativistic hyperbolic motion and the E x B drift with a different cell size on every axis
+(test_oracle_motion.py), the whole step against a brute-force dense-matrix composition on
+8 x 8 and 8 x 8 x 4 grids (test_oracle_dense.py), Table 1 re-fit, the self-force and kappa_r
+values of Sec. 2-3.
 The 5-pass current filter (named, not defined, in the paper) is pinned through its k-space
 symbol to the three filtered self-forces of Table 2.  The split axial operators ([k]_E1 != [k]_B1,
 Sec. 3) are pinned by the dispersion relation with the product of the two symbols, each side's
