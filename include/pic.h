@@ -118,6 +118,9 @@ typedef struct pic_config {
                                Sec. 3 correction), coef then defining only the E-side d+ ([k]_E1,
                                Faraday's law): the [k]_E1 != [k]_B1 solvers Sec. 3 allows, e.g.
                                with [k]_E1 [k]_B1 = [k1]_t^2.  Not supported by pic_adjoint_step. */
+    int precision;          /* arithmetic of fields, currents, offsets and momenta: 0 or 32 = FP32
+                               (the only one built); any other value is refused with PIC_ERR_ARG.
+                               Diagnostics always reduce in FP64. */
 } pic_config;
 
 /* ---- handle ------------------------------------------------------------------------
@@ -216,8 +219,10 @@ pic_status pic_gauss(pic_t* h, double* G, void* stream);
  * array until the process exits.  The call makes no cudaMalloc, cudaFree or other
  * allocating call.
  *   - Grids with more than PIC_STATIC_RHO_CELLS nodes are refused with PIC_ERR_ARG.
- *   - The handle's device must be current.  The first call on a device looks up the array's
- *     device address (cudaGetSymbolAddress) with that device current; later calls reuse it.
+ *   - The handle's device must be current.  pic_create looks up the array's device address
+ *     (cudaGetSymbolAddress, with the handle's device current) and keeps it in the handle; with
+ *     CUDA's lazy module loading that lookup is also what loads the array onto the device, so
+ *     its 8 MiB are placed when the handle is created, not by pic_gauss_static.
  *   - All calls share the single array.  It is cleared at the start of every call, so
  *     results never depend on an earlier call, but two calls that run at the same time on
  *     the GPU (different streams or handles) race on it and give wrong results: order them

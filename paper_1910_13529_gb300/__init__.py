@@ -48,7 +48,7 @@ class pic_config(ctypes.Structure):
         ("fit_wk", ctypes.c_double), ("fit_n", ctypes.c_double), ("shape", ctypes.c_int),
         ("moving_window", ctypes.c_int), ("inject_species", ctypes.c_int), ("inject_ppc", ctypes.c_int * 3),
         ("rho_bg", ctypes.c_double), ("sort_every", ctypes.c_int), ("current_filter", ctypes.c_int),
-        ("coef_b", ctypes.POINTER(ctypes.c_double)),
+        ("coef_b", ctypes.POINTER(ctypes.c_double)), ("precision", ctypes.c_int),
     ]
 
 

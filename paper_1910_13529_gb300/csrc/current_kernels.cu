@@ -152,6 +152,7 @@ struct CorrP {
 constexpr int kHL = PIC_MAX_HLEN;
 constexpr int kNWIN = 2 * kHL + 4;               // window floats (a multiple of 4: kHL even)
 static_assert(kNWIN % 4 == 0, "aligned windows");
+static_assert(kHL % 4 == 0, "s + kHL must be 16-byte aligned for the float4 filter stores");
 
 // floats of the correction's shared row: s[k] = J1[k - kHL] for k < nz4 + kNWIN
 __host__ __device__ constexpr int corr_floats(int nz) { return ((nz + 3) & ~3) + kNWIN; }
@@ -258,7 +259,8 @@ cudaError_t launch_rows(T* f, int nz, long long rows, int vec4, cudaStream_t s) 
 template <int NT>
 cudaError_t launch_fc(const CorrP& p, int vec4, cudaStream_t s) {
     const size_t smem = sizeof(float) * corr_floats(p.g.nz);
-    if (smem > 40 * 1024) {   // 48 KB less the static filter buffer
+    // the default limit is 48 KB for static and dynamic shared memory together
+    if (smem + sizeof(float) * (8 * NT + 16) > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(filter_correct_kernel<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;

@@ -67,6 +67,7 @@ struct pic_t {
     size_t ev_used = 0;
     long long launches[PIC_TIMING_N] = {0};
     float* adj_scratch = nullptr; // adjoint: B', E', W (7 N floats)
+    double* static_rho = nullptr; // device address of g_static_rho on this handle's device
     int fa_variant = 0;           // field-advance tile variant (pic_autotune)
     double fa_ms[PIC_MAX_TILE_VARIANTS] = {0};   // measured time per variant (ms), 0 = not measured
 };
@@ -76,11 +77,12 @@ namespace {
 char g_create_err[256] = "no error";
 
 // Fixed FP64 charge-density scratch of pic_gauss_static (no allocation).  In host code the
-// name g_static_rho is only a stand-in: its device address is looked up per device with
-// cudaGetSymbolAddress (with that device current) and kept here.
+// name g_static_rho is only a stand-in: pic_create looks up its device address with
+// cudaGetSymbolAddress, with the handle's device current, and keeps it in the handle.  Under
+// lazy module loading that lookup is what loads this module (and places the array) on the
+// device, so it happens when the handle is created, where allocation is expected, and never in
+// pic_gauss_static itself.
 __device__ __align__(256) double g_static_rho[PIC_STATIC_RHO_CELLS];
-constexpr int kMaxDevices = 64;
-double* g_static_rho_addr[kMaxDevices] = {nullptr};
 
 pic_status fail(pic_t* h, pic_status st, const char* fmt, ...) {
     char* dst = h ? h->err : g_create_err;
@@ -337,6 +339,8 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     if (c.solver != PIC_SOLVER_YEE && c.solver != PIC_SOLVER_CUSTOM)
         return fail(nullptr, PIC_ERR_ARG, "unknown solver %d", c.solver);
     if (c.shape != 1 && c.shape != 2) return fail(nullptr, PIC_ERR_ARG, "shape must be 1 or 2");
+    if (c.precision != 0 && c.precision != 32)
+        return fail(nullptr, PIC_ERR_ARG, "precision %d: only FP32 (0 or 32) kernels are built", c.precision);
     if (c.current_filter != PIC_FILTER_NONE && c.current_filter != PIC_FILTER_5PASS)
         return fail(nullptr, PIC_ERR_ARG, "unknown current_filter %d", c.current_filter);
     if (c.inject_species >= PIC_MAX_SPECIES) return fail(nullptr, PIC_ERR_ARG, "inject_species out of range");
@@ -414,6 +418,11 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     }
     cudaError_t e = cudaMemset(h->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->counts, 0, sizeof(int32_t) * PIC_MAX_SPECIES);
+    if (e == cudaSuccess) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_rho);
+        h->static_rho = static_cast<double*>(ptr);
+    }
     if (e != cudaSuccess) {
         snprintf(g_create_err, sizeof g_create_err, "cudaMemset: %s", cudaGetErrorString(e));
         pic_destroy(h);
@@ -646,13 +655,8 @@ pic_status pic_gauss_static(pic_t* h, double* G, void* stream) {
     if (dev != h->device)
         return fail(h, PIC_ERR_ARG, "pic_gauss_static: device %d is current, the handle lives on device %d", dev,
                     h->device);
-    if (dev < 0 || dev >= kMaxDevices) return fail(h, PIC_ERR_ARG, "pic_gauss_static: device index %d", dev);
-    if (!g_static_rho_addr[dev]) {
-        void* ptr = nullptr;
-        CK(h, cudaGetSymbolAddress(&ptr, g_static_rho), "cudaGetSymbolAddress of the fixed scratch");
-        g_static_rho_addr[dev] = static_cast<double*>(ptr);
-    }
-    double* rho = g_static_rho_addr[dev];
+    double* rho = h->static_rho;     // looked up by pic_create on this device
+    if (!rho) return fail(h, PIC_ERR_STATE, "pic_gauss_static: fixed scratch address not set");
     cudaStream_t s = (cudaStream_t)stream;
     CK(h, cudaMemsetAsync(rho, 0, sizeof(double) * h->g.ncell, s), "clear the fixed scratch");
     for (int i = 0; i < PIC_MAX_SPECIES; ++i) {

@@ -106,6 +106,11 @@ def test_new_options_are_validated_on_host(P):
     with pytest.raises(P.PicError) as ei:
         P.pic_create(c)
     assert ei.value.status == P.PIC_ERR_ARG and "current_filter" in P.pic_last_error()
+    c, keep = _cfg(P)
+    c.precision = 64                  # only the FP32 kernels are built
+    with pytest.raises(P.PicError) as ei:
+        P.pic_create(c)
+    assert ei.value.status == P.PIC_ERR_ARG and "precision" in P.pic_last_error()
     bad = [
         (dict(solver="custom", coef_b=F8), P.PIC_ERR_ARG),                  # no explicit E-side set
         (dict(solver="yee", coef_b=F8), P.PIC_ERR_ARG),                     # split needs the customised solver
