@@ -19,8 +19,11 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math",
-                           "-ffp-contract=off", SRC, "-o", tmp, "-lm"])
+    base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off", SRC, "-o", tmp]
+    # OpenMP (for the all-cores CPU baseline) when the compiler has it; plain otherwise
+    r = subprocess.run(base + ["-fopenmp", "-lm"], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -41,7 +41,21 @@ def lib():
         L.or_gauss.argtypes = [_ip, _dp, _dp, _dp, _dp, _dp]
         L.or_shift_z.argtypes = [_ip, ctypes.c_int, _dp]
         L.or_filter_z.argtypes = [_ip, ctypes.c_int, _dp]
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        L.or_get_threads.restype = ctypes.c_int
+        L.or_openmp.restype = ctypes.c_int
+        L.or_set_threads(1)          # one fixed summation order unless a caller asks for more
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's loops (OpenMP builds); returns the number in effect."""
+    lib().or_set_threads(int(n))
+    return lib().or_get_threads()
+
+
+def openmp() -> bool:
+    return bool(lib().or_openmp())
 
 
 def _d(a):

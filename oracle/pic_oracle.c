@@ -48,6 +48,35 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the loops below (OpenMP builds only).  The library starts single-threaded so that
+ * every test sees one fixed summation order; the CPU baseline raises it to time all cores.
+ * Loops over cells write disjoint outputs; the deposit and the charge density add into shared
+ * nodes with atomic updates. */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n < 1 ? 1 : n);
+#else
+    (void)n;
+#endif
+}
+int or_get_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+int or_openmp(void) {
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 typedef struct {
     int ndim, nz, nx, ny, M, shape, periodic_z;
@@ -120,6 +149,7 @@ static void faraday_half(const grid_t* g, const double* E, double* B) {
     const double *E1 = E, *E2 = E + N, *E3 = E + 2 * N;
     double *B1 = B, *B2 = B + N, *B3 = B + 2 * N;
     double h = 0.5 * g->dt;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->ny; ++k)
         for (int j = 0; j < g->nx; ++j)
             for (int i = 0; i < g->nz; ++i) {
@@ -138,6 +168,7 @@ static void ampere(const grid_t* g, double* E, const double* B, const double* J)
     long N = ncell(g);
     double *E1 = E, *E2 = E + N, *E3 = E + 2 * N;
     const double *B1 = B, *B2 = B + N, *B3 = B + 2 * N;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g->ny; ++k)
         for (int j = 0; j < g->nx; ++j)
             for (int i = 0; i < g->nz; ++i) {
@@ -173,7 +204,10 @@ void or_ampere(const int* ip, const double* dp, const double* C, double* E, cons
 /* Sec. 3 current correction: J1[i] <- sum_m h[m] J1[i-m], |m| <= hlen, J1 = 0 outside z. */
 void or_correct_j1(const int* ip, const double* h, int hlen, double* J) {
     grid_t g = mk(ip, (const double[4]){1, 1, 1, 1}, NULL);
+#pragma omp parallel
+    {
     double* row = (double*)malloc(sizeof(double) * g.nz);
+#pragma omp for collapse(2) schedule(static)
     for (int k = 0; k < g.ny; ++k)
         for (int j = 0; j < g.nx; ++j) {
             double* J1 = J + lin(&g, 0, j, k);
@@ -188,6 +222,7 @@ void or_correct_j1(const int* ip, const double* h, int hlen, double* J) {
             memcpy(J1, row, sizeof(double) * g.nz);
         }
     free(row);
+    }
 }
 
 /* B-spline particle shapes in cell units: linear (order 1) and quadratic (order 2). */
@@ -231,6 +266,7 @@ void or_gather(const int* ip, const double* dp, const double* E, const double* B
                long n, const double* xi, double* out) {
     grid_t g = mk(ip, dp, NULL);
     long N = ncell(&g);
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p)
         for (int c = 0; c < 6; ++c) {
             const double* f = c < 3 ? E + c * N : B + (c - 3) * N;
@@ -240,6 +276,7 @@ void or_gather(const int* ip, const double* dp, const double* E, const double* B
 
 /* Relativistic Boris push u^{n-1/2} -> u^{n+1/2}; eps = q dt / (2 m). */
 void or_boris(long n, const double* eb, double* u, double eps) {
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p) {
         const double* E = eb + 6 * p;
         const double* B = eb + 6 * p + 3;
@@ -264,6 +301,7 @@ void or_boris(long n, const double* eb, double* u, double eps) {
 void or_move(const int* ip, const double* dp, long n, const double* xi0, const double* u, double* xi1) {
     grid_t g = mk(ip, dp, NULL);
     double h[3] = {g.dz, g.dx, g.dy};
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p) {
         const double* v = u + 3 * p;
         double gam = sqrt(1.0 + v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
@@ -287,6 +325,7 @@ void or_deposit(const int* ip, const double* dp, long n, const double* xi0, cons
     double V = g.ndim == 3 ? g.dz * g.dx * g.dy : g.dz * g.dx;
     double hh[3] = {g.dz, g.dx, g.dy};
     enum { W = 8 };
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p) {
         const double* a0p = xi0 + 3 * p;
         const double* a1p = xi1 + 3 * p;
@@ -329,6 +368,7 @@ void or_deposit(const int* ip, const double* dp, long n, const double* xi0, cons
                         idx[a] = base[a] + ia; idx[b] = base[b] + ib; idx[c] = base[c] + ic;
                         if (idx[0] < 0 || idx[0] >= g.nz) continue;
                         int jj = wrap(idx[1], g.nx), kk = nd == 3 ? wrap(idx[2], g.ny) : 0;
+#pragma omp atomic
                         J[a * N + lin(&g, idx[0], jj, kk)] += fac * cum;
                     }
                 }
@@ -341,6 +381,7 @@ void or_deposit(const int* ip, const double* dp, long n, const double* xi0, cons
                               + 0.5 * S0[0][ia] * DS[1][ib] + DS[0][ia] * DS[1][ib] / 3.0;
                     int i = base[0] + ia;
                     if (i < 0 || i >= g.nz) continue;
+#pragma omp atomic
                     J[2 * N + lin(&g, i, wrap(base[1] + ib, g.nx), 0)] += fac * Wv;
                 }
         }
@@ -352,6 +393,7 @@ void or_deposit(const int* ip, const double* dp, long n, const double* xi0, cons
 void or_rho(const int* ip, const double* dp, long n, const double* xi, double Q, double* rho) {
     grid_t g = mk(ip, dp, NULL);
     double V = g.ndim == 3 ? g.dz * g.dx * g.dy : g.dz * g.dx;
+#pragma omp parallel for schedule(static)
     for (long p = 0; p < n; ++p) {
         const double* x = xi + 3 * p;
         int a0 = (int)floor(x[0]) - 2, b0 = (int)floor(x[1]) - 2;
@@ -364,6 +406,7 @@ void or_rho(const int* ip, const double* dp, long n, const double* xi, double Q,
                     if (a < 0 || a >= g.nz) continue;
                     double w = shape(g.shape, a - x[0]) * wx * wy;
                     if (w == 0.0) continue;
+#pragma omp atomic
                     rho[lin(&g, a, wrap(b, g.nx), g.ndim == 3 ? wrap(c, g.ny) : 0)] += Q / V * w;
                 }
             }
@@ -376,6 +419,7 @@ void or_gauss(const int* ip, const double* dp, const double* C, const double* E,
               const double* rho, double* G) {
     grid_t g = mk(ip, dp, C);
     long N = ncell(&g);
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < g.ny; ++k)
         for (int j = 0; j < g.nx; ++j)
             for (int i = 0; i < g.nz; ++i) {
@@ -395,7 +439,10 @@ void or_filter_z(const int* ip, int ncomp, double* F) {
     static const double w0[5] = {0.5, 0.5, 0.5, 0.5, 3.5};
     grid_t g = mk(ip, (const double[4]){1, 1, 1, 1}, NULL);
     long N = ncell(&g);
+#pragma omp parallel
+    {
     double* x = (double*)malloc(sizeof(double) * g.nz);
+#pragma omp for collapse(3) schedule(static)
     for (int c = 0; c < ncomp; ++c)
         for (int k = 0; k < g.ny; ++k)
             for (int j = 0; j < g.nx; ++j) {
@@ -412,6 +459,7 @@ void or_filter_z(const int* ip, int ncomp, double* F) {
                 }
             }
     free(x);
+    }
 }
 
 /* Moving window: every field array moves one cell towards -z, the front column becomes zero. */

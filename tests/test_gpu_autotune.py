@@ -91,3 +91,51 @@ def test_every_tile_variant_matches_oracle(nd, nz, nx, ny, solver, C, moving):
         assert sim.state()[1] == osim.shifts
         assert field_error(sim, osim) < 1e-5, v
         sim.close()
+
+
+CHUNK_CASES = [
+    # 2D x-march (variants 8..11: z segments of 448, 384, 960, 192 cells marching along x in
+    # chunks of at least 16 rows): nz = 1502 spans 2 to 8 segments with a ragged last one
+    # (nz % 4 = 2), nx = 80 gives 5 x chunks
+    (2, 1502, 80, 1, "custom", TABLE1, (8, 9, 10, 11)),
+    (2, 1502, 80, 1, "yee", None, (8, 9, 10, 11)),
+    # 3D y-march (6..9) and its prefetch ring (10, 11): ny = 20 gives 3 y chunks of >= 8 planes
+    (3, 261, 12, 20, "custom", TABLE1, (6, 7, 8, 9, 10, 11)),
+]
+
+
+@pytest.mark.parametrize("nd,nz,nx,ny,solver,C,variants", CHUNK_CASES)
+def test_marching_variants_across_chunks(nd, nz, nx, ny, solver, C, variants):
+    """The marching field-advance variants on grids large enough for several z segments and
+    several x (2D) or y (3D) chunks per launch, with and without the moving-window shift,
+    against the FP64 oracle after four steps."""
+    from oracle import fit
+    from paper_1910_13529_gb300 import pic_set_tuning
+
+    d = (0.5, 0.4, 0.45)
+    for moving in (False, True):
+        dt = 0.9 * fit.cfl_dt(d[0], [d[1]] + ([d[2]] if nd == 3 else []), C)
+        if moving:
+            dt = min(dt, 0.6 * d[0])
+        grid = dict(ndim=nd, nz=nz, nx=nx, ny=ny, dz=d[0], dx=d[1], dy=d[2], dt=dt, solver=solver, shape=1,
+                    moving_window=moving)
+        osim = oracle_sim(grid, [], coef=C)
+        rng = np.random.default_rng(nz + nx + ny)
+        init = [rng.normal(size=a.shape).astype(np.float32) for a in (osim.E, osim.B, osim.J)]
+        osim.E[:], osim.B[:], osim.J[:] = init
+        nsteps = 4
+        for _ in range(nsteps):
+            oc.field_advance(osim.g, osim.E, osim.B, osim.J)
+            osim.n += 1
+            if moving and oc.window_due(osim.n, osim.g.dt, osim.g.dz, osim.shifts):
+                osim.shift()
+        for v in variants:
+            sim = gpu_sim(grid, [], coef=C)
+            pic_set_tuning(sim.h, v)
+            for a, x in zip((sim.E, sim.B, sim.J), init):
+                a.copy_(torch.from_numpy(x))
+            for _ in range(nsteps):
+                sim.field_advance()
+            assert sim.state()[1] == osim.shifts
+            assert field_error(sim, osim) < 1e-5, (v, moving)
+            sim.close()

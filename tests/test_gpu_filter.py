@@ -103,10 +103,11 @@ def test_deposit_with_filter(name, nd, solver, shape, C):
     sim.close()
 
 
-@pytest.mark.parametrize("nz", [1000, 2048, 3001, 4100])
+@pytest.mark.parametrize("nz", [1000, 2048, 3001, 4100, 10180])
 def test_fused_filter_and_correction_on_long_rows(nz):
     """The fused kernel at every CTA size it takes (128 threads up to nz = 1024, 256 beyond) and over
-    several segments per row (nz > 2048), with and without 16-byte rows (nz % 4)."""
+    several segments per row (nz > 2048), with and without 16-byte rows (nz % 4); at nz = 10180 the
+    static and dynamic shared memory together just pass the 48 KB default limit."""
     grid = grid_of(2, nz, 4, 1, "custom", 2, C=TABLE1)
     sp = wl.random_particles(2, nz, 4, 1, 4000, seed=nz, u_scale=1.5, u_drift=(2.0, 0.3, -0.2), margin=6)
     sim = gpu_sim(grid, [sp], coef=TABLE1)
