@@ -1,16 +1,20 @@
 """Benchmark of the relativistic-beam EM PIC step on GB300.
 
-Workload: the 2D beam-in-plasma run -- grid 2048 (z) x 512 (x), dz = dx = 0.02 c/omega_p,
-dt = 0.9 x the customised-stencil stability limit, moving window at c, bi-Gaussian electron
-beam (sigma_z = 0.5, sigma_x = 0.2, gamma = 2e4 with 2% spread, 1e6 macro-particles) in a
-uniform plasma of 4 particles per cell, quadratic shapes, customised M = 16 axial stencil,
-FP32 fields and offsets; particles sorted by cell every 20 steps.  One step = gather + Boris
-+ Esirkepov deposition (fused) for both species, current correction, field advance, window
-shift / injection when due.
+Headline workload: the 3D beam in plasma -- grid 512 (z) x 256 (x) x 256 (y), dz = 0.02,
+dx = dy = 0.05 c/omega_p, dt = 0.9 x the customised-stencil stability limit, moving window at c,
+Gaussian electron beam (sigma_z = 0.5, sigma_r = 0.1, gamma = 2e4, 4e6 macro-particles) in a
+uniform plasma of 2 particles per cell (67,108,864), quadratic shapes, customised M = 16 axial
+stencil with the Sec. 3 current correction, FP32 fields and offsets; particles sorted by cell
+every 20 steps.  One step = gather + Boris + Esirkepov deposition (fused) for both species,
+current correction, field advance, window shift / injection when due.
 
-Reported: particle-pushes/s for the whole step (value), cell-updates/s, the HBM roofline of
-the dominant kernel (the fused particle kernel), an end-to-end number through the C ABI from
-pinned host buffers, and the FP64 oracle timed on the host cores (cpu_baseline).
+Reported on one JSON line: particle-pushes/s of the whole step (value, the median of repeated
+timed passes), cell-updates/s, the HBM roofline of the dominant kernel (the fused particle
+kernel), an end-to-end number through the C ABI from pinned host buffers, the FP64 oracle
+timed on the host cores on a stated sample (cpu_baseline), and under "secondary" the 2D beam in
+plasma (2048 x 512), the field advance alone on grids far above L2 (2D 8192 x 2048 Yee and
+M = 16, 3D 512 x 256 x 256 M = 16) with their HBM fractions, and the batched scan of 256
+independent single-particle runs against one launch sequence per instance.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: launched by torch.distributed.run, one independent replica per GPU (weak scaling,
@@ -20,6 +24,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import subprocess
 import sys
 import threading
@@ -34,15 +39,17 @@ BYTES_PER_PUSH_2D = 48          # read + write cell (4) + offsets (2 x 4) + u (3
 BYTES_PER_PUSH_3D = 56          # read + write cell (4) + offsets (3 x 4) + u (3 x 4)
 BYTES_PER_CELL_UPDATE = 60      # read E, B, J (9 x 4) + write E, B (6 x 4)
 METRIC = "cell-updates/s and particle-pushes/s (% HBM roofline) at <=1e-5 rel err vs FP64"
+REPEATS = 5                     # timed passes of --steps steps; the median is reported
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="headline only (profiling captures)")
     ap.add_argument("--small", action="store_true", help="reduced grid (profiling captures)")
     ap.add_argument("--fields-case", default=None, choices=["2d_yee", "2d_custom16", "3d_custom16"],
                     help="fields workload: run this grid only (profiling captures)")
@@ -51,31 +58,29 @@ def parse():
                     help="beam workloads with the 5-pass current filter along z (not the headline run)")
     ap.add_argument("--tile", type=int, default=None,
                     help="fields workload: force this field-advance tile variant instead of autotuning")
-    ap.add_argument("--workload", default="beam2d", choices=["beam2d", "beam3d", "batch", "fields"],
-                    help="beam2d: the bench workload; beam3d: the 3D 512 x 256 x 256 beam in plasma; "
-                         "batch: 256 independent single-particle runs, batched launch vs per-instance "
-                         "launches; fields: the field advance alone on grids above L2")
+    ap.add_argument("--workload", default="beam3d", choices=["beam2d", "beam3d", "batch", "fields"],
+                    help="beam3d: the headline 3D 512 x 256 x 256 beam in plasma; beam2d: the 2D 2048 x 512 "
+                         "beam in plasma; batch: 256 independent single-particle runs, batched launch vs "
+                         "per-instance launches; fields: the field advance alone on grids above L2")
     return ap.parse_args()
 
 
-def workload(args):
-    """(grid, species, name) of the timed run (with the 5-pass current filter under --filter)."""
-    (grid, sps), name = _workload(args)
-    if getattr(args, "filter", False):
-        grid["current_filter"] = True
-        name += "_filtered"
-    return (grid, sps), name
-
-
-def _workload(args):
+def workload(name, small=False, filt=False):
+    """(grid, species, workload name) of a beam run (with the 5-pass current filter under filt)."""
     from paper_1910_13529_gb300 import workloads as wl
-    if args.workload == "beam3d":
-        if args.small:
-            return wl.beam_plasma_3d(nz=256, nx=128, ny=128, n_beam=500_000), "beam_plasma_3d_small"
-        return wl.beam_plasma_3d(), "beam_plasma_3d"
-    if args.small:
-        return wl.beam_plasma(ndim=2, nz=512, nx=256, n_beam=250_000, behind_front=3.0), "beam_plasma_2d_small"
-    return wl.beam_plasma(), "beam_plasma_2d"
+    if name == "beam3d":
+        if small:
+            (grid, sps), wname = wl.beam_plasma_3d(nz=256, nx=128, ny=128, n_beam=500_000), "beam_plasma_3d_small"
+        else:
+            (grid, sps), wname = wl.beam_plasma_3d(), "beam_plasma_3d_512x256x256"
+    elif small:
+        (grid, sps), wname = wl.beam_plasma(ndim=2, nz=512, nx=256, n_beam=250_000), "beam_plasma_2d_small"
+    else:
+        (grid, sps), wname = wl.beam_plasma(), "beam_plasma_2d_2048x512"
+    if filt:
+        grid["current_filter"] = True
+        wname += "_filtered"
+    return grid, sps, wname
 
 
 def measured_peak():
@@ -91,8 +96,9 @@ def measured_peak():
 class ClockSampler:
     """nvidia-smi clock and throttle samples while the timed region runs."""
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
+        self.period_ms = period_ms
         self.lines = []
         self.proc = None
 
@@ -102,10 +108,12 @@ class ClockSampler:
                 ["nvidia-smi", "-i", str(self.index),
                  "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
                  "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "100"],
+                 "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms",
+                 str(self.period_ms)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)                       # first sample before the timed region
         except Exception:
             self.proc = None
         return self
@@ -142,37 +150,124 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_baseline(grid, sps, frac=0.25, seed=0, steps=2):
-    """FP64 oracle on the host: the full grid and a random fraction of the particles, `steps`
-    steps; returns (particle pushes per second, seconds, particles)."""
-    from oracle import core as oc
-    from oracle import fit
-    from paper_1910_13529_gb300 import workloads as wl
-    rng = np.random.default_rng(seed)
-    kappa = grid["dz"] / grid["dt"]
-    C = fit.fit_coefficients(kappa)
-    h = fit.correction_kernel(C, hlen=40)
-    g = oc.Grid(grid["ndim"], grid["nz"], grid["nx"], grid.get("ny", 1), grid["dz"], grid["dx"], grid["dy"],
-                grid["dt"], C=C, shape=grid["shape"])
-    species, n = [], 0
-    for sp in sps:
-        sel = rng.random(len(sp["iz"])) < frac
-        sub = {k: (v[..., sel] if isinstance(v, np.ndarray) and v.shape[-1] == len(sel) else v)
-               for k, v in sp.items()}
-        species.append(oc.Species(wl.xi_of(sub, grid["ndim"]), sub["u"].T.astype(np.float64), sp["q"], sp["m"],
-                                  sp["w"]))
-        n += int(sel.sum())
-    sim = oc.Sim(g, species, h=h, moving_window=True, filt=grid.get("current_filter", False))
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        sim.step()
-    dt = time.perf_counter() - t0
-    return n * steps / dt, dt, n
-
-
 def emit(obj):
     print(json.dumps(obj), flush=True)
 
+
+# ---------------------------------------------------------------- the FP64 oracle on the host ----
+
+def host_cpu():
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except Exception:
+        ncores = os.cpu_count() or 1
+    return model, ncores
+
+
+def oracle_step_sample(grid, sps, n_full, z_slab, threads, steps=1, seed=0):
+    """The FP64 oracle as it stands on a bounded piece of one step of the workload:
+      particles -- gather, Boris, move and Esirkepov deposit of the sampled particles on the full
+                   grid, scaled by n_full / n_sample;
+      fields    -- the Sec. 3 correction and the field advance on a z slab of z_slab cells with the
+                   full transverse grid, scaled by nz / z_slab (the cost is linear in the cells).
+    Returns a dict with the estimated full-step time and its parts (seconds)."""
+    from oracle import core as oc
+    from oracle import fit
+    from paper_1910_13529_gb300 import workloads as wl
+    used = oc.set_threads(threads)
+    nd = grid["ndim"]
+    kappa = grid["dz"] / grid["dt"]
+    C = fit.fit_coefficients(kappa)
+    h = fit.correction_kernel(C, hlen=40)
+    ny = grid.get("ny", 1)
+    g = oc.Grid(nd, grid["nz"], grid["nx"], ny, grid["dz"], grid["dx"], grid["dy"], grid["dt"], C=C,
+                shape=grid["shape"])
+    gs = oc.Grid(nd, z_slab, grid["nx"], ny, grid["dz"], grid["dx"], grid["dy"], grid["dt"], C=C,
+                 shape=grid["shape"])
+    E, B, J = g.zeros(), g.zeros(), g.zeros()
+    Es, Bs, Js = gs.zeros(), gs.zeros(), gs.zeros()
+    species = [oc.Species(wl.xi_of(sp, nd), sp["u"].T.astype(np.float64), sp["q"], sp["m"], sp["w"]) for sp in sps]
+    n = sum(len(s.xi) for s in species)
+    tp = tf = 0.0
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        for s in species:
+            eb = oc.gather(g, E, B, s.xi)
+            oc.boris(eb, s.u, s.q * g.dt / (2.0 * s.m))
+            xi1 = oc.move(g, s.xi, s.u)
+            oc.deposit(g, s.xi, xi1, s.u, s.Q, J)
+            s.xi = xi1
+        t1 = time.perf_counter()
+        oc.correct_j1(gs, h, Js)
+        oc.field_advance(gs, Es, Bs, Js)
+        t2 = time.perf_counter()
+        tp += t1 - t0
+        tf += t2 - t1
+    tp /= steps
+    tf /= steps
+    oc.set_threads(1)
+    t_part = tp * n_full / max(n, 1)
+    t_field = tf * grid["nz"] / z_slab
+    return dict(threads=used, n_sample=n, t_sample_s=tp + tf, t_particles_full_s=t_part, t_fields_full_s=t_field,
+                t_step_full_s=t_part + t_field)
+
+
+def cpu_baseline_3d(threads, frac, z_slab, steps=1, seed=0):
+    from paper_1910_13529_gb300 import workloads as wl
+    grid, sps, n_full = wl.beam_plasma_3d_sample(frac, seed=7 + seed)
+    r = oracle_step_sample(grid, sps, n_full, z_slab, threads, steps=steps, seed=seed)
+    cells = grid["nz"] * grid["nx"] * grid["ny"]
+    r.update(n_full=n_full, cells=cells, pushes_per_s=n_full / r["t_step_full_s"],
+             cell_updates_per_s=cells / r["t_fields_full_s"])
+    return r, grid
+
+
+def cpu_baseline_entry(r, grid, frac, z_slab, model, label):
+    return {"value": r["pushes_per_s"], "unit": "particle-pushes/s", "cores": r["threads"], "kind": "oracle",
+            "sample": f"{label}: one FP64 oracle step of the 512x256x256 beam in plasma on a sample -- "
+                      f"particle phase on {r['n_sample']} particles ({100 * frac:.2f}% of {r['n_full']}), "
+                      f"field phase (correction + field advance) on a {z_slab}x{grid['nx']}x{grid['ny']} z slab; "
+                      f"{r['t_sample_s']:.1f} s measured, scaled to the full step by particle count and by "
+                      f"cells",
+            "ms_per_step_full_estimate": 1e3 * r["t_step_full_s"],
+            "cell_updates_per_s": r["cell_updates_per_s"], "cpu_model": model}
+
+
+def run_reference(args, rank, world):
+    """The FP64 oracle on the host cores (all of them), on the headline configuration, each step a
+    bounded sample of the 3D workload scaled to the full step."""
+    if rank != 0:
+        return
+    model, ncores = host_cpu()
+    frac, z_slab = 0.004, 64
+    vals, ms = [], []
+    r = grid = None
+    for k in range(max(1, min(args.steps, 5))):
+        r, grid = cpu_baseline_3d(ncores, frac, z_slab, seed=k)
+        vals.append(r["pushes_per_s"])
+        ms.append(1e3 * r["t_step_full_s"])
+    value = float(np.median(vals))
+    cpu = cpu_baseline_entry(r, grid, frac, z_slab, model, f"{len(vals)} sampled steps, median")
+    cpu["value"] = value
+    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-pushes/s", "n_gpus": 0,
+          "steps": len(vals), "warmup": 0, "ms_per_step": float(np.median(ms)),
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+          "data": "synthetic (seeded beam + quiet-start plasma, sampled)",
+          "config": {"workload": "beam_plasma_3d_512x256x256", "grid": [512, 256, 256], "particles": r["n_full"]},
+          "cpu_baseline": cpu,
+          "e2e": {"value": value, "unit": "particle-pushes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+
+
+# ---------------------------------------------------------------- ncu traffic of the dominant kernel ----
 
 # ncu summaries committed under profiles/ that carry the DRAM traffic of a kernel class, with the
 # SHA-1 of the source file the capture was built from
@@ -182,10 +277,11 @@ TRAFFIC_SOURCES = {
 }
 
 
-def captured_traffic(kind, ndim):
+def captured_traffic(kind, ndim, units=None):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu summary, or
-    None when there is none or the kernel source has changed since the capture."""
-    import hashlib
+    None when there is none or the kernel source has changed since the capture.  A summary taken
+    on a reduced case states the particles of its captured step (units_per_step); the traffic is
+    then scaled to `units` (particles per step of the timed run) in proportion."""
     import re
     entry = TRAFFIC_SOURCES.get((kind, ndim))
     if entry is None:
@@ -200,7 +296,11 @@ def captured_traffic(kind, ndim):
     h = re.search(r"code_sha1:\s*([0-9a-f]{40})", text)
     if not m or not h or h.group(1) != digest:
         return None
-    return float(m.group(1))
+    t = float(m.group(1))
+    u = re.search(r"units_per_step:\s*([0-9.eE+]+)", text)
+    if u and units:
+        t *= units / float(u.group(1))
+    return t
 
 
 def code_sha1(source):
@@ -232,52 +332,214 @@ def aggregate(ms, pushes_per_step, steps, world, device=None):
     return ms_max, total, total / (ms_max / 1e3)
 
 
-def run_reference(args, rank, world):
-    if rank != 0:
-        return
-    (grid, sps), wname = workload(args)
-    n_total = sum(len(sp["iz"]) for sp in sps)
-    vals, times = [], []
-    # the oracle has nothing to warm up; at most three timed samples keep the run within minutes
-    for k in range(max(1, min(args.steps, 3))):
-        v, dt, n = oracle_baseline(grid, sps, frac=0.05, seed=k, steps=1)
-        vals.append(v)
-        times.append(dt)
-    value = float(np.median(vals))
-    sample = f"one FP64 oracle step on the full {grid['nz']}x{grid['nx']} grid with a 5% random sample " \
-             f"({n} of {n_total}) of the particles, single thread"
-    emit({"impl": "reference", "metric": METRIC, "value": value, "unit": "particle-pushes/s", "n_gpus": 0,
-          "steps": len(vals), "warmup": 0, "ms_per_step": 1e3 * float(np.median(times)),
-          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-          "data": "synthetic",
-          "config": {"workload": wname, "grid": [grid["nz"], grid["nx"]] + ([grid["ny"]] if grid["ndim"] == 3 else []),
-                     "particles": n_total},
-          "cpu_baseline": {"value": value, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
-                           "sample": sample},
-          "e2e": {"value": value, "unit": "particle-pushes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}})
+# ---------------------------------------------------------------- one beam-in-plasma run on the GPU ----
 
-
-def run_ours(args, rank, world, local_rank):
-    import torch
-    import torch.distributed as dist
-    from paper_1910_13529_gb300 import pic_timing, pic_timing_read
+def build_sim(grid, sps, dev, sort_every):
     from paper_1910_13529_gb300.runtime import Simulation
-
-    dev = torch.device(f"cuda:{local_rank}")
-    torch.cuda.set_device(dev)
-    (grid, sps), wname = workload(args)
     nd = grid["ndim"]
-    bpp = BYTES_PER_PUSH_3D if nd == 3 else BYTES_PER_PUSH_2D
     n0 = [len(sp["iz"]) for sp in sps]
     cap_extra = 200_000 if nd == 2 else 4_000_000    # injection between two compacting sorts
     kw = {k: grid[k] for k in ("ndim", "nz", "nx", "ny", "dz", "dx", "dy", "dt", "shape", "solver",
                                "moving_window", "inject_species", "inject_ppc", "rho_bg")}
     kw["current_filter"] = grid.get("current_filter", False)
-    sim = Simulation(device=str(dev), sort_every=args.sort_every, **kw)
+    sim = Simulation(device=str(dev), sort_every=sort_every, **kw)
     for s, sp in enumerate(sps):
         sim.add_species(s, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"],
                         cap=n0[s] + cap_extra)
-    stream = sim.stream
+    return sim, n0
+
+
+def timed_passes(sim, steps, repeats, barrier, dev):
+    """`repeats` passes of `steps` steps, each bracketed by a barrier and a synchronize, timed with
+    CUDA events on the stream the library launches on (torch's current stream).  Returns the ms of
+    each pass and the mean particle count over them."""
+    import torch
+    ms, counts = [], []
+    d = sim.diag()
+    counts.append(d["count"])
+    for _ in range(repeats):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(steps)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms.append(e0.elapsed_time(e1))
+        counts.append(sim.diag()["count"])
+    return ms, float(np.mean(counts))
+
+
+def kernel_breakdown(sim, steps):
+    """Per-kernel-class times (CUDA events around every launch, on the launch stream) from a separate
+    pass of the same length, so that the instrumentation stays out of the headline number."""
+    from paper_1910_13529_gb300 import pic_timing, pic_timing_read
+    c0 = sim.diag()["count"]
+    pic_timing(sim.h, 1)
+    sim.step(steps)
+    kms, kl = pic_timing_read(sim.h, sim.stream)
+    pic_timing(sim.h, 0)
+    c1 = sim.diag()["count"]
+    return kms, kl, 0.5 * (c0 + c1)
+
+
+def interior_gauss_change(sim, G0, margin):
+    G1 = sim.gauss()
+    d = (G1 - G0)[..., margin:-margin]
+    return float(d.abs().max().item())
+
+
+def run_beam_secondary(args, dev, wname_sel):
+    """The 2D beam in plasma (2048 x 512): pushes/s and the particle kernel's HBM fraction."""
+    import torch
+    grid, sps, wname = workload(wname_sel, filt=args.filter)
+    sim, n0 = build_sim(grid, sps, dev, args.sort_every)
+    tuned = sim.autotune()
+    sim.step(args.warmup)
+    torch.cuda.synchronize(dev)
+    ms, count = timed_passes(sim, args.steps, 3, lambda: torch.cuda.synchronize(dev), dev)
+    kms, kl, kcount = kernel_breakdown(sim, args.steps)
+    peak, kind = measured_peak()
+    med = float(np.median(ms))
+    bpp = BYTES_PER_PUSH_2D if grid["ndim"] == 2 else BYTES_PER_PUSH_3D
+    achieved = bpp * kcount * args.steps / (kms["particles"] / 1e3) / 1e9
+    cells = grid["nz"] * grid["nx"] * grid.get("ny", 1)
+    out = {"workload": wname, "particles": int(sum(n0)), "pushes_per_s": count * args.steps / (med / 1e3),
+           "ms_per_step": med / args.steps, "cell_updates_per_s": cells * args.steps / (med / 1e3),
+           "particle_kernel": {"achieved_GBps": achieved, "frac": achieved / peak, "peak_kind": kind,
+                               "ms_per_step": kms["particles"] / args.steps,
+                               "traffic": captured_traffic("particles", grid["ndim"])},
+           "field_advance_GBps": BYTES_PER_CELL_UPDATE * cells * args.steps / (kms["fields"] / 1e3) / 1e9,
+           "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "field_tile_variant": int(tuned[0]), "l2": "working set ~197 MB > 129 MB L2 (partly L2-resident)"}
+    sim.close()
+    return out
+
+
+def fields_cases(args, which=None):
+    """Field advance alone on grids far above L2: 2D 8192 x 2048 (Yee and customised M = 16) and
+    3D 512 x 256 x 256 (customised), cell-updates/s and the HBM fraction at 60 B/cell-update."""
+    import torch
+    from paper_1910_13529_gb300 import pic_get_tuning, pic_set_tuning, pic_timing, pic_timing_read
+    from paper_1910_13529_gb300 import workloads as wl
+    from paper_1910_13529_gb300.runtime import Simulation
+    dev = torch.device("cuda:0")
+    peak, kind = measured_peak()
+    cases = [("2d_8192x2048_yee", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dt=wl.DT_BEAM_2D, solver="yee")),
+             ("2d_8192x2048_custom16", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dt=wl.DT_BEAM_2D,
+                                            solver="custom", M=16)),
+             ("3d_512x256x256_custom16", dict(ndim=3, nz=512, nx=256, ny=256, dz=0.02, dx=0.05, dy=0.05,
+                                              dt=wl.DT_BEAM_3D, solver="custom", M=16))]
+    if which:
+        cases = [c for c in cases if c[0] == which]
+    out = {}
+    for name, cfg in cases:
+        sim = Simulation(device="cuda:0", **cfg)
+        gen = torch.Generator(device="cuda:0").manual_seed(1)
+        for t in (sim.E, sim.B, sim.J):
+            t.copy_(torch.randn(t.shape, device="cuda:0", generator=gen) * 1e-3)
+        if args.tile is None:
+            tuned = sim.autotune()
+        else:
+            pic_set_tuning(sim.h, args.tile)
+            tuned = pic_get_tuning(sim.h)
+        # pic_step without particles: J zeroed, (customised stencil) J1 corrected, field advance
+        # ping-ponging between the two buffers; the fields timing class holds the kernel alone
+        sim.step(args.warmup)
+        torch.cuda.synchronize(dev)
+        pic_timing(sim.h, 1)
+        K = max(args.steps, 20)
+        sim.step(K)
+        kms, kl = pic_timing_read(sim.h, sim.stream)
+        pic_timing(sim.h, 0)
+        cells = sim.nz * sim.nx * sim.ny
+        kern_ms = float(kms["fields"]) / max(int(kl["fields"]), 1)
+        gbs = BYTES_PER_CELL_UPDATE * cells / (kern_ms / 1e3) / 1e9
+        out[name] = {"cell-updates/s": cells / (kern_ms / 1e3), "kernel_ms": kern_ms, "achieved_GBps": gbs,
+                     "frac": gbs / peak, "peak_kind": kind, "tile_variant": int(tuned[0]),
+                     "variant_ms": [float(x) for x in tuned[1]],
+                     "l2": f"{cells * 60 / 1e6:.0f} MB moved per update > 129 MB L2"}
+        sim.close()
+    return out, K
+
+
+KAPPA_CFL_CUSTOM_2D = 1.632488686516034   # customised-stencil stability fixed point, r = 1
+
+
+def batch_configs(n=256, seed=4000):
+    """256 independent 2D single-particle vacuum runs: nz ~ U{128..1024}, nx ~ U{64..256},
+    log10 gamma ~ U[1, 5], dt = U[0.3, 0.99] x the instance's own solver limit, Yee or customised
+    (M = 16 fitted at the instance's kappa) by a fair coin, dz = dx = 0.05, linear shape."""
+    rng = np.random.default_rng(seed)
+    d = 0.05
+    out = []
+    for i in range(n):
+        nz = int(rng.integers(128, 1025))
+        nx = int(rng.integers(64, 257))
+        gamma = 10 ** rng.uniform(1, 5)
+        frac = rng.uniform(0.3, 0.99)
+        custom = bool(rng.integers(0, 2))
+        dt = frac * (d / KAPPA_CFL_CUSTOM_2D if custom else d / math.sqrt(2))
+        cfg = dict(ndim=2, nz=nz, nx=nx, dz=d, dx=d, dt=dt, shape=1, solver="custom" if custom else "yee", M=16)
+        out.append((cfg, gamma))
+    return out
+
+
+def batch_case(steps, warmup):
+    """Batched scan of 256 instances against one pic_step call sequence per instance (the same
+    kernels launched per instance), both timed with CUDA events on the same stream."""
+    import torch
+    from paper_1910_13529_gb300 import workloads as wl
+    from paper_1910_13529_gb300.runtime import Batch, Simulation
+    dev = torch.device("cuda:0")
+    cfgs = batch_configs()
+    batch = Batch([c for c, _ in cfgs])
+    singles = []
+    cells = 0
+    for i, (c, gamma) in enumerate(cfgs):
+        _, sps = wl.single_particle(nz=c["nz"], nx=c["nx"], d=c["dz"], dt_over_dz=c["dt"] / c["dz"], gamma=gamma,
+                                    z_cell=c["nz"] / 8, x_cell=c["nx"] / 2)
+        sp = sps[0]
+        batch.instances[i].add_species(0, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"])
+        s1 = Simulation(device="cuda:0", **c)
+        s1.add_species(0, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"])
+        singles.append(s1)
+        cells += c["nz"] * c["nx"]
+    batch.step(warmup)
+    for s1 in singles:
+        s1.step(warmup)
+    torch.cuda.synchronize(dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    with ClockSampler(0) as clk:
+        e0.record()
+        batch.step(steps)
+        e1.record()
+        for s1 in singles:
+            s1.step(steps)
+        e2.record()
+        torch.cuda.synchronize(dev)
+    tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    for s1 in singles:
+        s1.close()
+    batch.close()
+    return {"instances": len(cfgs), "cells_total": cells, "steps": steps,
+            "custom_instances": sum(1 for c, _ in cfgs if c["solver"] == "custom"),
+            "batched_cell_updates_per_s": cells * steps / (tb / 1e3),
+            "per_instance_cell_updates_per_s": cells * steps / (ts / 1e3),
+            "speedup_batched_over_per_instance": ts / tb, "ms_batched": tb, "ms_per_instance": ts,
+            "clocks": clk.summary()}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1910_13529_gb300 import encode_cells, pic_bind_species
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    grid, sps, wname = workload(args.workload, small=args.small, filt=args.filter)
+    nd = grid["ndim"]
+    bpp = BYTES_PER_PUSH_3D if nd == 3 else BYTES_PER_PUSH_2D
+    sim, n0 = build_sim(grid, sps, dev, args.sort_every)
     tuned = sim.autotune()           # field-advance tile shape for this grid (timed, cached)
 
     def barrier():
@@ -286,27 +548,19 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize(dev)
 
     sim.step(args.warmup)
-    d0 = sim.diag()
+    margin = (16 + 24 + 2) + (5 if grid.get("current_filter") else 0)
+    G0 = sim.gauss()
     barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
-        ev0.record()
-        sim.step(args.steps)
-        ev1.record()
-        torch.cuda.synchronize(dev)
+        ms_list, count = timed_passes(sim, args.steps, REPEATS, barrier, dev)
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    d1 = sim.diag()
-    # per-kernel-class times (CUDA events around every launch, on the launch stream) from a second
-    # timed pass of the same length, so that the instrumentation stays out of the headline number
-    pic_timing(sim.h, 1)
-    sim.step(args.steps)
-    kms, klaunch = pic_timing_read(sim.h, stream)
-    pic_timing(sim.h, 0)
-    d2 = sim.diag()
+    ms = float(np.median(ms_list))
+    dG = interior_gauss_change(sim, G0, margin)
+    rho_max = sim.diag()["rho_max"]
+    del G0
+    kms, klaunch, kcount = kernel_breakdown(sim, args.steps)
     barrier()
-    pushes_per_step = 0.5 * (d0["count"] + d1["count"])
-    ms_max, total_pushes, value = aggregate(ms, pushes_per_step, args.steps, world, dev)
+    ms_max, total_pushes, value = aggregate(ms, count, args.steps, world, dev)
     cells = grid["nz"] * grid["nx"] * grid.get("ny", 1)
     cell_rate = cells * args.steps * world / (ms_max / 1e3)
 
@@ -314,11 +568,14 @@ def run_ours(args, rank, world, local_rank):
     dom = max(kms, key=kms.get)
     peak, peak_kind = measured_peak()
     if dom == "particles":
-        algo = bpp * 0.5 * (d1["count"] + d2["count"]) * args.steps
+        algo = bpp * kcount * args.steps
+        units_per_step = kcount
     else:
         algo = BYTES_PER_CELL_UPDATE * cells * args.steps
+        units_per_step = cells
     achieved = algo / (kms[dom] / 1e3) / 1e9
-    fa_gbs = BYTES_PER_CELL_UPDATE * cells * args.steps / (kms["fields"] / 1e3) / 1e9 if kms["fields"] else None
+    # DRAM bytes per launch of the class (ncu), scaled from a reduced capture by particles per step
+    traffic = captured_traffic(dom, nd, units=kcount if dom == "particles" else None)
 
     # end to end through the C ABI from pinned host buffers: upload the initial state, run the
     # steps, download the final fields and particles
@@ -327,7 +584,6 @@ def run_ours(args, rank, world, local_rank):
         d = sim.species[s]
         host.append({k: torch.empty_like(d[k], device="cpu").pin_memory() for k in ("cell", "off", "u")})
         host[-1]["cell"].fill_(-1)
-        from paper_1910_13529_gb300 import encode_cells
         n = n0[s]
         host[-1]["cell"][:n] = torch.from_numpy(encode_cells(sp["iz"], sp["ix"], sp["iy"], grid["nz"], grid["nx"]))
         host[-1]["off"][:, :n] = torch.from_numpy(sp["off"][: grid["ndim"]])
@@ -336,7 +592,6 @@ def run_ours(args, rank, world, local_rank):
     hB = torch.zeros_like(sim.B, device="cpu").pin_memory()
     out = [{k: torch.empty_like(v).pin_memory() for k, v in h.items()} for h in host]
     oE, oB = torch.empty_like(hE).pin_memory(), torch.empty_like(hB).pin_memory()
-    from paper_1910_13529_gb300 import pic_bind_species
     h2d = sum(t.numel() * t.element_size() for h in host for t in h.values()) + 2 * hE.numel() * 4
     d2h = h2d
     barrier()
@@ -363,167 +618,83 @@ def run_ours(args, rank, world, local_rank):
     t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = total_pushes / (float(t.item()) / 1e3)
+    e2e_value = sum(n0) * world * args.steps / (float(t.item()) / 1e3)
+    working = (sum(sim.species[s]["cap"] for s in sim.species) * (bpp // 2) + cells * 4 * (6 + 6 + 3)) / 1e6
+    sim.close()
+    del host, out, hE, hB, oE, oB
+    torch.cuda.empty_cache()
 
+    secondary = {"cell-updates/s": cell_rate, "ms_per_pass": ms_list,
+                 "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+                 "kernel_launches_per_step": {k: v / args.steps for k, v in klaunch.items()},
+                 "gauss_change_interior_max": dG, "rho_max": rho_max}
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 2:
-        v, dt, n = oracle_baseline(grid, sps, frac=0.5, steps=2)
-        cpu = {"value": v, "unit": "particle-pushes/s", "cores": 1, "kind": "oracle",
-               "sample": f"two FP64 oracle steps, full {grid['nz']}x{grid['nx']} grid, 50% random particle "
-                         f"sample ({n} particles), {dt:.1f} s single-threaded"}
+    if world == 1 and not args.no_secondary and args.workload == "beam3d" and not args.small:
+        secondary["beam_plasma_2d"] = run_beam_secondary(args, dev, "beam2d")
+        fc, kf = fields_cases(args)
+        secondary["field_advance_large_grids"] = fc
+        secondary["batched_scan"] = batch_case(max(args.steps, 20), max(args.warmup, 3))
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 3 and not args.small:
+        model, ncores = host_cpu()
+        r1, g1 = cpu_baseline_3d(1, 0.001, 16)
+        rn, gn = cpu_baseline_3d(ncores, 0.004, 64)
+        cpu = cpu_baseline_entry(rn, gn, 0.004, 64, model, f"all {rn['threads']} host threads")
+        cpu["single_thread"] = cpu_baseline_entry(r1, g1, 0.001, 16, model, "1 thread")
+        cpu["nproc"] = ncores
     if rank == 0:
-        launches = int(sum(klaunch.values()))
-        working = (sum(sim.species[s]["cap"] for s in sim.species) * (bpp // 2) + cells * 4 * (6 + 6 + 3)) / 1e6
+        launches = int(sum(klaunch.values())) * REPEATS
         emit({"metric": METRIC, "value": value, "unit": "particle-pushes/s", "n_gpus": world,
               "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic (seeded beam + quiet-start plasma)",
               "config": {"workload": wname,
                          "grid": [grid["nz"], grid["nx"]] + ([grid["ny"]] if nd == 3 else []),
-                         "particles": int(sum(n0)), "solver": "custom M=16",
+                         "particles": int(sum(n0)), "solver": "custom M=16 + Sec. 3 correction",
                          "shape": "quadratic", "moving_window": True, "sort_every": args.sort_every,
-                         "current_filter": "5-pass" if kw["current_filter"] else "none",
+                         "current_filter": "5-pass" if grid.get("current_filter") else "none",
+                         "timing": f"median of {REPEATS} passes of {args.steps} steps",
                          "l2": f"inputs larger than L2 (working set {working:.0f} MB > 129 MB)",
                          "parallelism": f"{world} independent replica(s)",
                          "field_tile_variant": int(tuned[0])},
-              "secondary": {"cell-updates/s": cell_rate,
-                            "field_advance_GBps": fa_gbs,
-                            "kernel_ms": kms, "kernel_launches": klaunch},
               "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": captured_traffic(dom, nd),
-                           "algorithmic_bytes_per_unit": bpp if dom == "particles" else BYTES_PER_CELL_UPDATE},
+                           "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                           "algorithmic_bytes_per_unit": bpp if dom == "particles" else BYTES_PER_CELL_UPDATE,
+                           "units_per_step": units_per_step,
+                           "launches_per_step": klaunch[dom] / args.steps,
+                           "kernel_ms_per_step": kms[dom] / args.steps},
               "cpu_baseline": cpu,
               "e2e": {"value": e2e_value, "unit": "particle-pushes/s", "h2d_bytes_per_step": h2d / args.steps,
                       "d2h_bytes_per_step": d2h / args.steps},
               "gpu_launches": launches,
               "clocks": clk.summary(),
-              "diag": {"count": d1["count"], "shifts": d1["shifts"], "gauss_max": d1["gauss_max"],
-                       "rho_max": d1["rho_max"]}})
-    sim.close()
-
-
-KAPPA_CFL_CUSTOM_2D = 1.632488686516034   # customised-stencil stability fixed point, r = 1
-
-
-def batch_configs(n=256, seed=4000):
-    """256 independent 2D single-particle vacuum runs: nz ~ U{128..1024}, nx ~ U{64..256},
-    log10 gamma ~ U[1, 5], dt = U[0.3, 0.99] x the instance's own solver limit, Yee or customised
-    (M = 16 fitted at the instance's kappa) by a fair coin, dz = dx = 0.05, linear shape."""
-    import math
-    rng = np.random.default_rng(seed)
-    d = 0.05
-    out = []
-    for i in range(n):
-        nz = int(rng.integers(128, 1025))
-        nx = int(rng.integers(64, 257))
-        gamma = 10 ** rng.uniform(1, 5)
-        frac = rng.uniform(0.3, 0.99)
-        custom = bool(rng.integers(0, 2))
-        dt = frac * (d / KAPPA_CFL_CUSTOM_2D if custom else d / math.sqrt(2))
-        cfg = dict(ndim=2, nz=nz, nx=nx, dz=d, dx=d, dt=dt, shape=1, solver="custom" if custom else "yee", M=16)
-        out.append((cfg, gamma))
-    return out
+              "secondary": secondary})
 
 
 def run_batch(args):
-    import torch
-    from paper_1910_13529_gb300 import workloads as wl
-    from paper_1910_13529_gb300.runtime import Batch, Simulation
-    dev = torch.device("cuda:0")
-    cfgs = batch_configs()
-    batch = Batch([c for c, _ in cfgs])
-    singles = []
-    cells = 0
-    for i, (c, gamma) in enumerate(cfgs):
-        _, sps = wl.single_particle(nz=c["nz"], nx=c["nx"], d=c["dz"], dt_over_dz=c["dt"] / c["dz"], gamma=gamma,
-                                    z_cell=c["nz"] / 8, x_cell=c["nx"] / 2)
-        sp = sps[0]
-        batch.instances[i].add_species(0, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"])
-        s1 = Simulation(device="cuda:0", **c)
-        s1.add_species(0, sp["iz"], sp["ix"], sp["iy"], sp["off"], sp["u"], sp["q"], sp["m"], sp["w"])
-        singles.append(s1)
-        cells += c["nz"] * c["nx"]
-    K = args.steps
-    batch.step(args.warmup)
-    for s1 in singles:
-        s1.step(args.warmup)
-    torch.cuda.synchronize(dev)
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    with ClockSampler(0) as clk:
-        e0.record()
-        batch.step(K)
-        e1.record()
-        for s1 in singles:
-            s1.step(K)
-        e2.record()
-        torch.cuda.synchronize(dev)
-    tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
-    value = cells * K / (tb / 1e3)
-    emit({"metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": 1, "steps": K, "warmup": args.warmup,
-          "ms_per_step": tb / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+    r = batch_case(args.steps, args.warmup)
+    emit({"metric": METRIC, "value": r["batched_cell_updates_per_s"], "unit": "cell-updates/s", "n_gpus": 1,
+          "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_batched"] / args.steps,
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
           "data": "synthetic (seeded instance parameters)",
-          "config": {"workload": "batched_vacuum_scan", "instances": len(cfgs), "cells_total": cells,
-                     "custom_instances": sum(1 for c, _ in cfgs if c["solver"] == "custom")},
-          "secondary": {"per_instance_launches_cell_updates_per_s": cells * K / (ts / 1e3),
-                        "speedup_batched_over_per_instance": ts / tb, "ms_batched": tb, "ms_per_instance": ts},
-          "clocks": clk.summary()})
-    for s1 in singles:
-        s1.close()
-    batch.close()
+          "config": {"workload": "batched_vacuum_scan", "instances": r["instances"], "cells_total": r["cells_total"],
+                     "custom_instances": r["custom_instances"]},
+          "secondary": r, "clocks": r["clocks"]})
 
 
 def run_fields(args):
-    """Field advance alone on grids far above L2: 2D 8192 x 2048 (Yee and customised M = 16) and
-    3D 512 x 256 x 256 (customised), cell-updates/s and the HBM fraction at 60 B/cell-update."""
-    import torch
-    from paper_1910_13529_gb300 import pic_timing, pic_timing_read, workloads as wl
-    from paper_1910_13529_gb300.runtime import Simulation
-    dev = torch.device("cuda:0")
-    peak, kind = measured_peak()
-    cases = [("2d_8192x2048_yee", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dt=wl.DT_BEAM_2D, solver="yee")),
-             ("2d_8192x2048_custom16", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dt=wl.DT_BEAM_2D,
-                                            solver="custom", M=16)),
-             ("3d_512x256x256_custom16", dict(ndim=3, nz=512, nx=256, ny=256, dz=0.02, dx=0.05, dy=0.05,
-                                              dt=wl.DT_BEAM_3D, solver="custom", M=16))]
+    tag = None
     if args.fields_case:
         tag = {"2d_yee": "2d_8192x2048_yee", "2d_custom16": "2d_8192x2048_custom16",
                "3d_custom16": "3d_512x256x256_custom16"}[args.fields_case]
-        cases = [c for c in cases if c[0] == tag]
-    out = {}
-    for name, cfg in cases:
-        sim = Simulation(device="cuda:0", **cfg)
-        gen = torch.Generator(device="cuda:0").manual_seed(1)
-        for t in (sim.E, sim.B, sim.J):
-            t.copy_(torch.randn(t.shape, device="cuda:0", generator=gen) * 1e-3)
-        if args.tile is None:
-            tuned = sim.autotune()
-        else:
-            from paper_1910_13529_gb300 import pic_get_tuning, pic_set_tuning
-            pic_set_tuning(sim.h, args.tile)
-            tuned = pic_get_tuning(sim.h)
-        # pic_step without particles: J zeroed, (customised stencil) J1 corrected, field advance
-        # ping-ponging between the two buffers; the fields timing class holds the kernel alone
-        sim.step(args.warmup)
-        torch.cuda.synchronize(dev)
-        pic_timing(sim.h, 1)
-        K = max(args.steps // 10, 20)
-        sim.step(K)
-        kms, kl = pic_timing_read(sim.h, sim.stream)
-        pic_timing(sim.h, 0)
-        cells = sim.nz * sim.nx * sim.ny
-        kern_ms = float(kms["fields"]) / max(int(kl["fields"]), 1)
-        gbs = 60 * cells / (kern_ms / 1e3) / 1e9
-        out[name] = {"cell-updates/s": cells / (kern_ms / 1e3), "kernel_ms": kern_ms, "achieved_GBps": gbs,
-                     "frac": gbs / peak, "tile_variant": int(tuned[0]), "variant_ms": [float(x) for x in tuned[1]]}
-        sim.close()
+    out, K = fields_cases(args, tag)
     best = out.get("2d_8192x2048_custom16", next(iter(out.values())))
     emit({"metric": METRIC, "value": best["cell-updates/s"], "unit": "cell-updates/s", "n_gpus": 1,
           "steps": K, "warmup": args.warmup, "ms_per_step": best["kernel_ms"], "higher_is_better": True,
           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded random fields)",
           "config": {"workload": "field_advance_large_grids", "l2": "inputs larger than L2"},
-          "roofline": {"bound": "hbm", "kernel": "field_advance", "achieved": best["achieved_GBps"], "peak": peak,
-                       "unit": "GB/s", "frac": best["frac"], "peak_kind": kind, "traffic": None,
-                       "algorithmic_bytes_per_unit": 60},
+          "roofline": {"bound": "hbm", "kernel": "field_advance", "achieved": best["achieved_GBps"],
+                       "peak": measured_peak()[0], "unit": "GB/s", "frac": best["frac"], "peak_kind": best["peak_kind"],
+                       "traffic": None, "algorithmic_bytes_per_unit": 60},
           "cases": out})
 
 

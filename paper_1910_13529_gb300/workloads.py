@@ -176,3 +176,42 @@ def rigid_line(nz=1024, nx=256, d=0.05, dt_over_dz=0.25, gamma=1e4, n=64, z_cell
     u[0] = math.sqrt(gamma * gamma - 1.0)
     grid = dict(ndim=2, nz=nz, nx=nx, ny=1, dz=d, dx=d, dy=d, dt=dt_over_dz * d, shape=1)
     return grid, [species(cz, cx, np.zeros(n, np.int64), np.stack([oz, ox]), u, -1.0, 1.0, 1.0 / n)]
+
+
+def quiet_plasma_sample(ndim, nz, nx, ny, ppc, d, frac, seed, density=1.0):
+    """A random fraction of the quiet-start plasma of quiet_plasma() (same lattice, same weight),
+    drawn without building the whole lattice: lattice indices in the order (k, j, i, a, b, c)."""
+    pz, px = ppc[0], ppc[1]
+    py = ppc[2] if ndim == 3 else 1
+    nyy = ny if ndim == 3 else 1
+    total = nyy * nx * nz * pz * px * py
+    rng = np.random.default_rng(seed)
+    idx = np.unique(rng.integers(0, total, max(int(frac * total), 1)))
+    r = idx
+    c, r = r % py, r // py
+    b, r = r % px, r // px
+    a, r = r % pz, r // pz
+    i, r = r % nz, r // nz
+    j, k = r % nx, r // nx
+    offs = [((a + 0.5) / pz).astype(np.float32), ((b + 0.5) / px).astype(np.float32)]
+    if ndim == 3:
+        offs.append(((c + 0.5) / py).astype(np.float32))
+    n = len(idx)
+    V = d[0] * d[1] * (d[2] if ndim == 3 else 1.0)
+    w = density * V / (pz * px * py)
+    return species(i, j, k, np.stack(offs), np.zeros((3, n), np.float32), -1.0, 1.0, w), total
+
+
+def beam_plasma_3d_sample(frac, seed=7):
+    """A random fraction of the particles of beam_plasma_3d() (plasma and beam alike), with the
+    full run's grid: for timing the FP64 oracle on a bounded piece of the 3D workload."""
+    grid, _ = beam_plasma_3d(nz=8, nx=8, ny=8, n_beam=8)         # grid parameters only
+    nz, nx, ny = 512, 256, 256
+    grid.update(nz=nz, nx=nx, ny=ny)
+    d = (grid["dz"], grid["dx"], grid["dy"])
+    plasma, n_plasma = quiet_plasma_sample(3, nz, nx, ny, grid["inject_ppc"], d, frac, seed)
+    beam = gaussian_beam(3, nz, nx, ny, d, 4_000_000, 0.5, 0.1, 2e4, 0.0, 100.0, nz * d[0] - 3.0, 1003)
+    keep = np.random.default_rng(seed + 1).random(len(beam["iz"])) < frac
+    beam = species(beam["iz"][keep], beam["ix"][keep], beam["iy"][keep], beam["off"][:, keep], beam["u"][:, keep],
+                   beam["q"], beam["m"], beam["w"])
+    return grid, [plasma, beam], n_plasma + 4_000_000
