@@ -112,7 +112,8 @@ def test_rigid_line(nz, nx, n, steps):
     e = errors(sim, osim)
     report(f"rigid_line_{nz}x{nx}_M4", steps, e)
     assert e["E"]["max_rel"] < TOL and e["B"]["max_rel"] < TOL
-    assert e["u"]["max_rel"] == 0.0 and e["x_cells_max_abs"] < TOL
+    # rigid: momenta stay at their initial values up to the denormal noise of eps ~ 1e-32
+    assert e["u"]["max_rel"] < 1e-12 and e["x_cells_max_abs"] < TOL
     sim.close()
 
 
