@@ -140,6 +140,13 @@ const char* pic_last_error(const pic_t* h);
  * Appendix C least-squares fit of C_1..C_M to the Sec. 3 target [k1]_t with kappa = dz/dt,
  * constraint sum (2l-1) C_l = 1 (p = 2), weight w_k1 = wk, order n.  C_out: M doubles.   */
 pic_status pic_fit_coefficients(double kappa, int M, double wk, double n, double* C_out);
+/* The B side of a split pair (Sec. 3: [k]_E1 != [k]_B1 with [k]_E1 [k]_B1 = [k1]_t^2): the same fit
+ * with the target [k1]_t^2 / [k]_E1, [k]_E1 the operator of the ME coefficients CE (CE = {1}: a Yee
+ * E side).  The pair keeps the fundamental-zone Cerenkov cancellation of [k]_1 = [k1]_t (the E1
+ * numerator [w]_t^2 - [k]_E1 [k]_B1 of Eq. EM); the transverse force E2 - beta B3 then carries the
+ * factor [w]_t / [k]_B1 != 1 of Eq. EM.  C_out: M doubles; use as pic_config coef_b with coef = CE
+ * (padded with zeros to M).                                                                   */
+pic_status pic_fit_coefficients_b(double kappa, int M, double wk, double n, const double* CE, int ME, double* C_out);
 /* Sec. 3 correction taps: impulse response of 1/P, P(phi) = sum_l C_l sin((2l-1)phi/2)/sin(phi/2),
  * h_out: 2*hlen+1 doubles, centre at index hlen.  PIC_ERR_ARG if P has a zero.          */
 pic_status pic_correction_taps(const double* C, int M, int hlen, double* h_out);

@@ -37,14 +37,20 @@ def constraint_matrix(M: int, p: int) -> np.ndarray:
 
 
 def fit_coefficients(kappa: float, M: int = 16, p: int = 2, w_k1: float = 0.6, n: float = 10.0,
-                     nq: int = 1000) -> np.ndarray:
-    """Solve the Appendix C Lagrange system for C_1..C_M with target [k1]_t (Sec. 3)."""
+                     nq: int = 1000, CE=None) -> np.ndarray:
+    """Solve the Appendix C Lagrange system for C_1..C_M with target [k1]_t (Sec. 3).
+
+    With CE (coefficients of an E-side operator [k]_E1) the target is [k1]_t^2 / [k]_E1: the B side
+    of a pair with [k]_E1 [k]_B1 = [k1]_t^2, the [k]_E1 != [k]_B1 option of Sec. 3."""
     x, wq = leggauss(nq)
     k = 0.25 * (x + 1.0)          # map [-1, 1] -> [0, 1/2]
     wq = 0.25 * wq
     w = np.exp(-math.log(2.0) * (2.0 * k / w_k1) ** n)
     s = np.array([np.sin((2 * l - 1) * math.pi * k) for l in range(1, M + 1)])
     target = kappa / math.pi * np.sin(math.pi * k / kappa)
+    if CE is not None:
+        ke = sum(c * np.sin((2 * l - 1) * math.pi * k) for l, c in enumerate(CE, start=1)) / math.pi
+        target = target * target / ke
     A = 2.0 / math.pi ** 2 * (s * (w * wq)) @ s.T
     b = 2.0 / math.pi * (s * (w * wq)) @ target
     Mc = constraint_matrix(M, p)

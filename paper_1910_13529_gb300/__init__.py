@@ -24,7 +24,8 @@ DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "co
              "status", "interior"]
 
 # exported symbols declared in include/pic.h
-EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_correction_taps",
+EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_fit_coefficients_b",
+           "pic_correction_taps",
            "pic_cfl_dt", "pic_cfl_dt_split", "pic_get_coefficients", "pic_get_coefficients_b", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
            "pic_deposit", "pic_field_advance", "pic_step", "pic_filter_current", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
            "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
@@ -63,6 +64,8 @@ def _load():
         "pic_destroy": ([vp], ctypes.c_int),
         "pic_last_error": ([vp], ctypes.c_char_p),
         "pic_fit_coefficients": ([ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp], ctypes.c_int),
+        "pic_fit_coefficients_b": ([ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int,
+                                    dp], ctypes.c_int),
         "pic_correction_taps": ([dp, ctypes.c_int, ctypes.c_int, dp], ctypes.c_int),
         "pic_cfl_dt": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, ctypes.c_int, dp],
                        ctypes.c_int),
@@ -149,6 +152,13 @@ def pic_last_error(h=None):
 def pic_fit_coefficients(kappa, M=16, wk=0.0, n=0.0):
     C = np.zeros(M)
     _check(lib.pic_fit_coefficients(float(kappa), int(M), float(wk), float(n), _dptr(C)))
+    return C
+
+
+def pic_fit_coefficients_b(kappa, CE, M=16, wk=0.0, n=0.0):
+    CE = np.ascontiguousarray(CE, dtype=np.float64)
+    C = np.zeros(M)
+    _check(lib.pic_fit_coefficients_b(float(kappa), int(M), float(wk), float(n), _dptr(CE), len(CE), _dptr(C)))
     return C
 
 

@@ -79,7 +79,10 @@ int solve(std::vector<ld>& A, std::vector<ld>& b, int n) {
 // k_g = 2 pi/dz, solved through the bordered (Lagrange) system.  The system is very
 // ill-conditioned (the high-order sines are nearly dependent where the weight lives), so the
 // quadrature and the solve run in extended precision.
-int fit_coefficients(double kappa, int M, double wk, double n, double* C) {
+// The target is (kappa/pi) sin(pi k/kappa) ([k1]_t, Sec. 3); with CE given (ME coefficients of an
+// E-side operator) it is [k1]_t^2 / [k]_E1, the B side of a pair with [k]_E1 [k]_B1 = [k1]_t^2
+// (the [k]_E1 != [k]_B1 solvers Sec. 3 allows).
+static int fit_target(double kappa, int M, double wk, double n, const double* CE, int ME, double* C) {
     if (M < 1 || M > PIC_MAX_M || !(kappa > 0.0)) return 1;
     if (wk <= 0.0) wk = 0.6;
     if (n <= 0.0) n = 10.0;
@@ -93,6 +96,13 @@ int fit_coefficients(double kappa, int M, double wk, double n, double* C) {
         ld k = 0.25L * (gx[q] + 1.0L);
         ld wq = 0.25L * gw[q] * std::exp(-std::log(2.0L) * std::pow(2.0L * k / (ld)wk, (ld)n));
         ld target = (ld)kappa / pi * std::sin(pi * k / (ld)kappa);
+        if (CE) {
+            ld ke = 0.0L;                    // [k]_E1 in units of k_g: sum_l C_l sin((2l-1) pi k) / pi
+            for (int l = 0; l < ME; ++l) ke += (ld)CE[l] * std::sin((2 * l + 1) * pi * k);
+            ke /= pi;
+            if (!(std::fabs(ke) > 0.0L)) continue;     // k = 0: no weight in the quadrature
+            target = target * target / ke;
+        }
         ld s[PIC_MAX_M];
         for (int l = 0; l < M; ++l) s[l] = std::sin((2 * l + 1) * pi * k);
         for (int i = 0; i < M; ++i) {
@@ -108,6 +118,15 @@ int fit_coefficients(double kappa, int M, double wk, double n, double* C) {
     if (solve(K, rhs, N)) return 1;
     for (int l = 0; l < M; ++l) C[l] = (double)rhs[l];
     return 0;
+}
+
+int fit_coefficients(double kappa, int M, double wk, double n, double* C) {
+    return fit_target(kappa, M, wk, n, nullptr, 0, C);
+}
+
+int fit_coefficients_b(double kappa, int M, double wk, double n, const double* CE, int ME, double* C) {
+    if (!CE || ME < 1 || ME > PIC_MAX_M) return 1;
+    return fit_target(kappa, M, wk, n, CE, ME, C);
 }
 
 // Sec. 3 correction: taps of the inverse of P(phi) = P_0 + 2 sum_m P_m cos(m phi),

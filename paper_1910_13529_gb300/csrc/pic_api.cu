@@ -299,6 +299,12 @@ pic_status pic_fit_coefficients(double kappa, int M, double wk, double n, double
     return fit_coefficients(kappa, M, wk, n, C_out) ? PIC_ERR_ARG : PIC_OK;
 }
 
+pic_status pic_fit_coefficients_b(double kappa, int M, double wk, double n, const double* CE, int ME,
+                                  double* C_out) {
+    if (!C_out || !CE || M < 1 || M > PIC_MAX_M || ME < 1 || ME > PIC_MAX_M || !(kappa > 0.0)) return PIC_ERR_ARG;
+    return fit_coefficients_b(kappa, M, wk, n, CE, ME, C_out) ? PIC_ERR_ARG : PIC_OK;
+}
+
 pic_status pic_correction_taps(const double* C, int M, int hlen, double* h_out) {
     if (!C || !h_out || M < 1 || M > PIC_MAX_M || hlen < 0 || hlen > 4096) return PIC_ERR_ARG;
     return correction_taps(C, M, hlen, h_out) ? PIC_ERR_ARG : PIC_OK;

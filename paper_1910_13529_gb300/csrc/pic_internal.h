@@ -160,6 +160,7 @@ cudaError_t launch_grad_corr(const GridP& g, int M, const float* W, const float*
 
 // ---- host math (host_math.cpp) ----
 int fit_coefficients(double kappa, int M, double wk, double n, double* C);
+int fit_coefficients_b(double kappa, int M, double wk, double n, const double* CE, int ME, double* C);
 int correction_taps(const double* C, int M, int hlen, double* h);
 double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M);
 // with the E-side (CE) and B-side (CB) symbols: max of their product; -1 if the product is negative

@@ -151,3 +151,42 @@ def test_refusals():
         with pytest.raises(P.PicError):
             Simulation(device="cuda:0", ndim=2, nz=64, nx=8, dz=0.5, dx=0.4, dt=0.05, solver="custom",
                        coef=kw.get("coef", CE), coef_b=g["coef_b"])
+
+
+def test_product_matched_pair_transverse_force():
+    """The product-matched pair of Sec. 3 (Yee E side, B side fitted by the library to
+    [k1]_t^2 / [k]_Yee, pic_fit_coefficients_b) on a beta -> 1 particle (gamma = 1e7, kappa = 4,
+    r = 1, quadratic shape, moving window), 1600 steps against the FP64 oracle; the B3~/E2~ ratio
+    measured on the GPU fields follows Eq. EM ([w]_t / [k]_B1, about -3.6% from 1 at k1 dz >= 0.7)."""
+    from tforce_util import band_means, measured_ratio, predicted_ratio
+
+    kappa, nz, nx, steps = 4.0, 384, 48, 1600
+    CB = P.pic_fit_coefficients_b(kappa, [1.0], M=16)
+    assert np.abs(CB - fit.fit_coefficients(kappa, M=16, CE=[1.0])).max() < 1e-6
+    CE = np.zeros(16)
+    CE[0] = 1.0
+    sp = wl.species([nz - 130], [nx // 2], [0], np.array([[0.0], [0.5]], np.float32),
+                    np.array([[1e7], [0.0], [0.0]], np.float32), 1.0, 1.0, 1.0)
+    grid = dict(ndim=2, nz=nz, nx=nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=1.0 / kappa, solver="custom", shape=2,
+                coef_b=list(CB), moving_window=True)
+    sim = gpu_sim(grid, [sp], coef=CE)
+    osim = oracle_sim(grid, [sp], coef=CE)
+    sim.step(steps)
+    prev = oc.set_threads(4)
+    try:
+        for _ in range(steps):
+            osim.step()
+    finally:
+        oc.set_threads(1)
+    assert field_error(sim, osim) < TOL
+    g = osim.g
+    E = sim.E.double().cpu().numpy()
+    B = sim.B.double().cpu().numpy()
+    oc.faraday_half(g, E, B)
+    step, shifts, pend = sim.state()
+    zp = osim.species[0].xi[0, 0]
+    j0 = nx // 2
+    ks, r = measured_ratio(E[1, 0, j0 + 3, :], B[2, 0, j0 + 3, :], zp, kappa)
+    m, p = band_means(ks, r, predicted_ratio(ks, kappa, CB))
+    assert abs(m - p) < 5e-3 and m < -0.03, (m, p)
+    sim.close()
