@@ -534,6 +534,30 @@ def batch_case(steps, warmup):
             "clocks": clk.summary()}
 
 
+def tuning_case(iters=15):
+    """The stencil-tuning run: 1024 x 256 vacuum, a rigid line of 64 electrons at gamma = 1e4,
+    kappa = 4, loss = field energy behind the line after 500 steps, M = 4 coefficients from the
+    Appendix C fit, adjoint with checkpoints every 50 steps; projected descent (tuning.py)."""
+    import time as _t
+    import torch
+    from paper_1910_13529_gb300 import pic_fit_coefficients
+    from paper_1910_13529_gb300 import workloads as wl
+    from paper_1910_13529_gb300.runtime import StencilLoss
+    from paper_1910_13529_gb300.tuning import tune_coefficients
+    grid, sps = wl.rigid_line()
+    C0 = pic_fit_coefficients(grid["dz"] / grid["dt"], M=4)
+    problem = StencilLoss(grid, sps, nsteps=500, every=50)
+    torch.cuda.synchronize()
+    t0 = _t.perf_counter()
+    hist = tune_coefficients(problem, C0, iters=iters)
+    torch.cuda.synchronize()
+    dt = _t.perf_counter() - t0
+    return {"grid": [1024, 256], "steps": 500, "checkpoint_every": 50, "C_appendix_c_fit": list(map(float, C0)),
+            "C_tuned": list(map(float, hist["C_final"])), "loss": list(map(float, hist["loss"])),
+            "loss_ratio": float(hist["loss"][-1] / hist["loss"][0]), "evaluations": hist["evals"],
+            "s_per_loss_and_gradient": dt / hist["evals"]}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -640,6 +664,7 @@ def run_ours(args, rank, world, local_rank):
         fc, kf = fields_cases(args)
         secondary["field_advance_large_grids"] = fc
         secondary["batched_scan"] = batch_case(max(args.steps, 20), max(args.warmup, 3))
+        secondary["stencil_tuning"] = tuning_case()
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 3 and not args.small:
         model, ncores = host_cpu()
         r1, g1 = cpu_baseline_3d(1, 0.001, 16)

@@ -142,3 +142,19 @@ def test_full_size_gradient_matches_stored_fp64_finite_differences():
     L, g = problem.loss_and_grad(C)
     assert L == pytest.approx(L_ref, rel=1e-5)
     assert np.max(np.abs(g - g_ref)) < 1e-4 * np.max(np.abs(g_ref))
+
+
+def test_stencil_tuning_lowers_the_wake_energy():
+    """Projected descent with the adjoint gradient (tuning.tune_coefficients) from the Appendix C
+    fit: the loss falls at every accepted step, the consistency constraint stays exact, and the
+    loss reported at the tuned coefficients is the FP64 oracle's."""
+    from paper_1910_13529_gb300.tuning import tune_coefficients
+    grid, sps, nsteps = _problem(60)
+    problem = StencilLoss(grid, sps, nsteps=nsteps, every=10)
+    hist = tune_coefficients(problem, C4, iters=6)
+    losses = hist["loss"]
+    assert len(losses) >= 3 and all(b < a for a, b in zip(losses, losses[1:]))
+    w = 2 * np.arange(1, 5) - 1.0
+    assert abs(w @ hist["C_final"] - 1.0) < 1e-12
+    assert fit.cfl_dt(grid["dz"], [grid["dx"]], hist["C_final"]) > grid["dt"]
+    assert hist["loss_final"] == pytest.approx(_oracle_loss(hist["C_final"], grid, sps, nsteps), rel=1e-5)
