@@ -467,24 +467,13 @@ def fields_cases(args, which=None):
     return out, K
 
 
-KAPPA_CFL_CUSTOM_2D = 1.632488686516034   # customised-stencil stability fixed point, r = 1
-
-
 def batch_configs(n=256, seed=4000):
-    """256 independent 2D single-particle vacuum runs: nz ~ U{128..1024}, nx ~ U{64..256},
-    log10 gamma ~ U[1, 5], dt = U[0.3, 0.99] x the instance's own solver limit, Yee or customised
-    (M = 16 fitted at the instance's kappa) by a fair coin, dz = dx = 0.05, linear shape."""
-    rng = np.random.default_rng(seed)
-    d = 0.05
+    """The 256 instances of the batched vacuum scan (workloads.batched_vacuum_scan); the customised
+    instances fit their M = 16 coefficients in pic_create at their own kappa."""
+    from paper_1910_13529_gb300 import workloads as wl
     out = []
-    for i in range(n):
-        nz = int(rng.integers(128, 1025))
-        nx = int(rng.integers(64, 257))
-        gamma = 10 ** rng.uniform(1, 5)
-        frac = rng.uniform(0.3, 0.99)
-        custom = bool(rng.integers(0, 2))
-        dt = frac * (d / KAPPA_CFL_CUSTOM_2D if custom else d / math.sqrt(2))
-        cfg = dict(ndim=2, nz=nz, nx=nx, dz=d, dx=d, dt=dt, shape=1, solver="custom" if custom else "yee", M=16)
+    for grid, gamma in wl.batched_vacuum_scan(n, seed):
+        cfg = {k: grid[k] for k in ("ndim", "nz", "nx", "dz", "dx", "dt", "shape", "solver", "M")}
         out.append((cfg, gamma))
     return out
 
@@ -523,6 +512,8 @@ def batch_case(steps, warmup):
         e2.record()
         torch.cuda.synchronize(dev)
     tb, ts = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    from paper_1910_13529_gb300 import pic_batch_get_tuning
+    variants, vms = pic_batch_get_tuning(batch.b)
     for s1 in singles:
         s1.close()
     batch.close()
@@ -531,6 +522,8 @@ def batch_case(steps, warmup):
             "batched_cell_updates_per_s": cells * steps / (tb / 1e3),
             "per_instance_cell_updates_per_s": cells * steps / (ts / 1e3),
             "speedup_batched_over_per_instance": ts / tb, "ms_batched": tb, "ms_per_instance": ts,
+            "field_variant_per_class": {"yee": variants[0], "custom16": variants[3]},
+            "field_variant_ms": {"yee": list(map(float, vms[0])), "custom16": list(map(float, vms[3]))},
             "clocks": clk.summary()}
 
 

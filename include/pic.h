@@ -311,7 +311,11 @@ pic_status pic_set_tuning(pic_t* h, int variant);
  * grid, dt, stencil (Yee or customised, own coefficients), shape and one particle species.
  * pic_batch_step advances all of them with one launch per kernel class and step (J zero,
  * gather/push/deposit, filter, correction, field advance per stencil class), recorded once into a
- * CUDA graph (two steps, one per field-buffer parity) and replayed on the caller's stream.
+ * CUDA graph (two steps, one per field-buffer parity) and replayed on the caller's stream.  The
+ * field advance of a stencil class walks one work list over all its instances' tiles; the first
+ * pic_batch_step after binding times the batched tile variants (one cell per thread, register-
+ * blocked, and in 2D x-marching z segments) on the bound fields and keeps the fastest per class
+ * (that call synchronises the stream).
  * Instance i is an ordinary handle (pic_batch_instance) for binding and diagnostics; bind its
  * fields and species before the first pic_batch_step.  After pic_batch_step returns (on the
  * stream) the bound field arrays of every instance hold the current fields.              */
@@ -319,6 +323,10 @@ typedef struct pic_batch_t pic_batch_t;
 pic_status pic_batch_create(const pic_config* cfgs, int n, pic_batch_t** out);
 pic_status pic_batch_instance(pic_batch_t* b, int i, pic_t** h);
 pic_status pic_batch_step(pic_batch_t* b, int nsteps, void* stream);
+/* Field-advance variant chosen per stencil class (variant[4]: classes M <= 1, 4, 8, 16; -1 when
+ * the class has no instance; 0 one cell per thread, 1 register-blocked, 2 x-marching) and the
+ * timed ms of one launch per variant (ms[12], 3 per class; 0 when not timed). */
+pic_status pic_batch_get_tuning(const pic_batch_t* b, int* variant, double* ms);
 pic_status pic_batch_destroy(pic_batch_t* b);
 
 #ifdef __cplusplus

@@ -29,7 +29,7 @@ EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients"
            "pic_cfl_dt", "pic_cfl_dt_split", "pic_get_coefficients", "pic_get_coefficients_b", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
            "pic_deposit", "pic_field_advance", "pic_step", "pic_filter_current", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
            "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
-           "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy",
+           "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy", "pic_batch_get_tuning",
            "pic_autotune", "pic_get_tuning", "pic_set_tuning", "pic_adjoint_step",
            "pic_set_state", "pic_get_next_id"]
 TIMING_KEYS = ["particles", "deposit", "correction", "fields", "sort", "window", "diag", "filter"]
@@ -99,6 +99,7 @@ def _load():
         "pic_get_tuning": ([vp, ip, dp, ip], ctypes.c_int),
         "pic_set_tuning": ([vp, ctypes.c_int], ctypes.c_int),
         "pic_adjoint_step": ([vp, vp, vp, vp, vp, vp, vp, vp], ctypes.c_int),
+        "pic_batch_get_tuning": ([vp, ip, dp], ctypes.c_int),
         "pic_set_state": ([vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
         "pic_get_next_id": ([vp, i64p], ctypes.c_int),
     }
@@ -307,6 +308,14 @@ def pic_get_next_id(h):
     n = ctypes.c_int64()
     _check(lib.pic_get_next_id(h, ctypes.byref(n)), h)
     return n.value
+
+
+def pic_batch_get_tuning(b):
+    """(variant per stencil class [4], ms per class and variant (4, 3)) of the batched field advance."""
+    v = (ctypes.c_int * 4)()
+    ms = np.zeros(12)
+    _check(lib.pic_batch_get_tuning(b, v, _dptr(ms)))
+    return list(v), ms.reshape(4, 3)
 
 
 def pic_batch_create(cfgs):

@@ -276,6 +276,12 @@ __device__ __forceinline__ void cp_async16(float* dst, const float* src, bool va
     const int n = valid ? 16 : 0;
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
+// 4-byte copy with zero fill (valid = false reads nothing): rows that are not 16-byte aligned
+__device__ __forceinline__ void cp_async4z(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = valid ? 4 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_all;\n" ::: "memory");
 }
@@ -303,14 +309,14 @@ __device__ __forceinline__ void stage_rows(float* dst, int cstride, const float*
 #pragma unroll
             for (int c = 0; c < 3; ++c) cp_async16(d + c * cstride, f[c] + o, in);
         } else {
+            // rows not 16-byte aligned: element copies, asynchronous as well
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float a[4];
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    a[j] = (gz + j >= 0 && gz + j < g.nz) ? __ldg(f[c] + row + gz + j) : 0.f;
-                sts4(d + c * cstride, a);
-            }
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = gz + j >= 0 && gz + j < g.nz;
+                    cp_async4z(d + c * cstride + j, f[c] + (in ? row + gz + j : 0), in);
+                }
         }
     }
 }
@@ -369,7 +375,7 @@ __device__ __forceinline__ void advance_tile_rb(const FieldP& p, int tz, int tx,
     stage_rows<NDIM, T::RX1>(sB, T::SB, p.Bin, p.Bin + N, p.Bin + 2 * N, T::RY1 * T::RX1, WB, z0 - T::H1, x0, y0,
                              -1, g, vec);
     stage_rows<NDIM, T::RX2>(sJ, T::SJ, p.J1, p.J2, p.J3, T::RY2 * T::RX2, WJ, z0 - T::H2, x0, y0, 0, g, vec);
-    if (vec) cp_async_wait_all();
+    cp_async_wait_all();
     __syncthreads();
 
     // ---- stage 1: B^{n+1/2} in place, rows x in [-1, TX] (y in [-1, TY]), z in [-H1, TZ+H1) --
@@ -566,14 +572,14 @@ __device__ __forceinline__ void stage_plane(float* dst, int cstride, const float
 #pragma unroll
             for (int c = 0; c < 3; ++c) cp_async16(d + c * cstride, f[c] + o, in);
         } else {
+            // rows not 16-byte aligned: element copies, asynchronous as well
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float a[4];
+            for (int c = 0; c < 3; ++c)
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    a[j] = (gz + j >= 0 && gz + j < g.nz) ? __ldg(f[c] + row + gz + j) : 0.f;
-                sts4(d + c * cstride, a);
-            }
+                for (int j = 0; j < 4; ++j) {
+                    const bool in = gz + j >= 0 && gz + j < g.nz;
+                    cp_async4z(d + c * cstride + j, f[c] + (in ? row + gz + j : 0), in);
+                }
         }
     }
 }
@@ -895,16 +901,13 @@ __device__ __forceinline__ void march2_bnew_store(const FieldP& p, const float* 
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev_group() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-template <int MAXM, int TZ, int NT>
-__global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int xc) {
+// One z segment [z0, z0 + TZ) of rows xa .. xb - 1 (the body of the x-marching kernels).
+template <int MAXM, int TZ>
+__device__ __forceinline__ void march2_segment(const FieldP& p, int z0, int xa, int xb, float* sm) {
     using T = March2T<MAXM, TZ>;
-    extern __shared__ float4 smem4[];
-    float* sm = reinterpret_cast<float*>(smem4);
     const GridP& g = p.g;
     const long long N = g.ncell;
     const bool vec = p.vec4 != 0;
-    const int z0 = blockIdx.x * TZ;
-    const int xa = blockIdx.y * xc, xb = min(xa + xc, g.nx);
     auto Eslot = [&](int i) { return sm + i * T::SE; };
     auto Bslot = [&](int i) { return sm + 4 * T::SE + i * T::SB; };
     auto Jslot = [&](int i) { return sm + 4 * T::SE + 3 * T::SB + i * T::SJ; };
@@ -920,7 +923,7 @@ __global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int 
         stage_plane(Jslot(i), T::WJ, p.J1, p.J2, p.J3, 1, T::WJ, z0 - T::H2, wrapi(x, g.nx), 0, 0, g, vec);
     };
     auto landed_all = [&]() {
-        if (vec) cp_async_wait_all();
+        cp_async_wait_all();
         __syncthreads();
     };
     // prologue: B^{n+1/2}(xa-1), B^{n+1/2}(xa), E^{n+1}(xa), and the first prefetch
@@ -943,13 +946,13 @@ __global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int 
     stageE(ef, xa + 2);
     stageB(bf, xa + 1);
     stageJ(jf, xa + 1);
-    if (vec) cp_async_commit_group();
+    cp_async_commit_group();
     for (int k = xa; k < xb; ++k) {
         // the next step's rows, while this step computes
         stageE(eg, k + 3);
         stageB(bg, k + 2);
         stageJ(jg, k + 2);
-        if (vec) {
+        {
             cp_async_commit_group();
             cp_async_wait_prev_group();             // this step's rows (committed one step earlier)
         }
@@ -973,7 +976,33 @@ __global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int 
         jf = jg;
         jg = t;
     }
-    if (vec) cp_async_wait_all();                   // no copy may outlive the CTA's shared memory
+    cp_async_wait_all();                   // no copy may outlive the CTA's shared memory
+}
+
+template <int MAXM, int TZ, int NT>
+__global__ void __launch_bounds__(NT) field_advance_march2_kernel(FieldP p, int xc) {
+    extern __shared__ float4 smem4[];
+    const int z0 = blockIdx.x * TZ;
+    const int xa = blockIdx.y * xc, xb = min(xa + xc, p.g.nx);
+    march2_segment<MAXM, TZ>(p, z0, xa, xb, reinterpret_cast<float*>(smem4));
+}
+
+// Many independent 2D grids: a persistent grid walks a work list of (instance, z segment, first
+// row, last row + 1) items; inst[2 i + parity] holds instance i's parameters for this step's
+// buffer direction.  Every item is the x-marching segment of field_advance_march2_kernel.
+template <int MAXM, int TZ, int NT>
+__global__ void __launch_bounds__(NT) field_advance_march2_batch_kernel(const FieldP* __restrict__ inst,
+                                                                        const int4* __restrict__ work, int nwork,
+                                                                        int parity) {
+    extern __shared__ float4 smem4[];
+    __shared__ FieldP sp;
+    for (int w = blockIdx.x; w < nwork; w += gridDim.x) {
+        const int4 it = work[w];
+        __syncthreads();                        // the previous item is done with sp
+        if (threadIdx.x == 0) sp = inst[2 * it.x + parity];
+        __syncthreads();
+        march2_segment<MAXM, TZ>(sp, it.y, it.z, it.w, reinterpret_cast<float*>(smem4));
+    }
 }
 
 // Ring variant of the y-march: the planes a step needs next (E^n(k+3), B^n(k+2), J(k+2)) are
@@ -1015,7 +1044,7 @@ __global__ void __launch_bounds__(NT) field_advance_march_ring_kernel(FieldP p, 
     stageB(0, ya - 1);
     stageB(1, ya);
     stageJ(0, ya);
-    if (vec) cp_async_wait_all();
+    cp_async_wait_all();
     __syncthreads();
     march_bhalf<MAXM, TZ, TX>(p, Bslot(0), Eslot(0), Eslot(1), z0);
     march_bhalf<MAXM, TZ, TX>(p, Bslot(1), Eslot(1), Eslot(2), z0);
@@ -1028,12 +1057,12 @@ __global__ void __launch_bounds__(NT) field_advance_march_ring_kernel(FieldP p, 
     stageE(ef, ya + 2);
     stageB(bf, ya + 1);
     stageJ(jf, ya + 1);
-    if (vec) cp_async_commit_group();
+    cp_async_commit_group();
     for (int k = ya; k < yb; ++k) {
         stageE(eg, k + 3);
         stageB(bg, k + 2);
         stageJ(jg, k + 2);
-        if (vec) {
+        {
             cp_async_commit_group();
             cp_async_wait_prev_group();             // this step's planes (committed one step earlier)
         }
@@ -1057,7 +1086,7 @@ __global__ void __launch_bounds__(NT) field_advance_march_ring_kernel(FieldP p, 
         jf = jg;
         jg = t;
     }
-    if (vec) cp_async_wait_all();
+    cp_async_wait_all();
 }
 
 template <int MAXM, int TZ, int TX, int NT>
@@ -1086,7 +1115,7 @@ __global__ void __launch_bounds__(NT) field_advance_march_kernel(FieldP p, int y
         stage_plane(sJ, T::PJ, p.J1, p.J2, p.J3, T::RX2, T::WJ, z0 - T::H2, x0, 0, wrapi(y, g.ny), g, vec);
     };
     auto landed = [&]() {
-        if (vec) cp_async_wait_all();
+        cp_async_wait_all();
         __syncthreads();
     };
     // prologue: B^{n+1/2}(ya-1), B^{n+1/2}(ya), E^{n+1}(ya)
@@ -1158,6 +1187,31 @@ __global__ void __launch_bounds__(256) field_advance_batch_kernel(const FieldP* 
     const int l = slocal;
     const int tz = l % ntz, tx = (l / ntz) % ntx, ty = NDIM == 3 ? l / (ntz * ntx) : 0;
     advance_tile<NDIM, MAXM, TZ, TX, TY>(sp, tz, tx, ty, smem);
+}
+
+// The same tile list with the register-blocked tile (advance_tile_rb).
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+__global__ void __launch_bounds__(256, 2) field_advance_rb_batch_kernel(const FieldP* __restrict__ inst,
+                                                                        const int* __restrict__ tile_start, int ninst,
+                                                                        int parity) {
+    extern __shared__ float4 smem4[];
+    __shared__ FieldP sp;
+    __shared__ int slocal;
+    if (threadIdx.x == 0) {
+        const int t = blockIdx.x;
+        int lo = 0, hi = ninst - 1;          // last instance whose first tile is <= t
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (tile_start[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        slocal = t - tile_start[lo];
+        sp = inst[2 * lo + parity];
+    }
+    __syncthreads();
+    const int ntz = (sp.g.nz + TZ - 1) / TZ, ntx = (sp.g.nx + TX - 1) / TX;
+    const int l = slocal;
+    const int tz = l % ntz, tx = (l / ntz) % ntx, ty = NDIM == 3 ? l / (ntz * ntx) : 0;
+    advance_tile_rb<NDIM, MAXM, TZ, TX, TY>(sp, tz, tx, ty, reinterpret_cast<float*>(smem4));
 }
 
 template <int NDIM, int MAXM, int TZ, int TX, int TY>
@@ -1288,11 +1342,72 @@ cudaError_t launch_fa_batch(const FieldP* inst, const int* tile_start, int ninst
 
 }  // namespace
 
+template <int NDIM, int MAXM, int TZ, int TX, int TY>
+cudaError_t launch_fa_rb_batch(const FieldP* inst, const int* tile_start, int ninst, int total, int parity,
+                               cudaStream_t s) {
+    using T = TileRB<NDIM, MAXM, TZ, TX, TY>;
+    auto k = field_advance_rb_batch_kernel<NDIM, MAXM, TZ, TX, TY>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k<<<(unsigned)total, 256, T::smem_bytes, s>>>(inst, tile_start, ninst, parity);
+    return cudaGetLastError();
+}
+
+template <int MAXM, int TZ, int NT>
+cudaError_t launch_fa_march2_batch(const FieldP* inst, const int4* work, int nwork, int parity, cudaStream_t s) {
+    using T = March2T<MAXM, TZ>;
+    auto k = field_advance_march2_batch_kernel<MAXM, TZ, NT>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)T::smem_bytes);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2048 / NT ? 2048 / NT : per_sm);
+    const int grid = nwork < nsm * per_sm ? nwork : nsm * per_sm;
+    if (grid <= 0) return cudaSuccess;
+    k<<<grid, NT, T::smem_bytes, s>>>(inst, work, nwork, parity);
+    return cudaGetLastError();
+}
+
 // Tiles of one grid in the batched field advance (same tile shapes as launch_field_advance_batch).
+// Batched 2D x-march: z segments of MARCH2_BATCH_TZ cells (64 threads), rows in chunks.
+cudaError_t launch_field_advance_march2_batch(const FieldP* inst, const int4* work, int nwork, int maxm, int parity,
+                                              cudaStream_t s) {
+    if (nwork <= 0) return cudaSuccess;
+    if (maxm <= 1) return launch_fa_march2_batch<1, MARCH2_BATCH_TZ, 64>(inst, work, nwork, parity, s);
+    if (maxm <= 4) return launch_fa_march2_batch<4, MARCH2_BATCH_TZ, 64>(inst, work, nwork, parity, s);
+    if (maxm <= 8) return launch_fa_march2_batch<8, MARCH2_BATCH_TZ, 64>(inst, work, nwork, parity, s);
+    return launch_fa_march2_batch<16, MARCH2_BATCH_TZ, 64>(inst, work, nwork, parity, s);
+}
+
 int field_tiles(int ndim, int maxm, int nz, int nx, int ny) {
     (void)maxm;
     if (ndim == 2) return ((nz + 127) / 128) * ((nx + 7) / 8);
     return ((nz + 63) / 64) * ((nx + 3) / 4) * ((ny + 3) / 4);
+}
+
+cudaError_t launch_field_advance_rb_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,
+                                          int ndim, int maxm, int parity, cudaStream_t s) {
+    if (ninst <= 0 || total_tiles <= 0) return cudaSuccess;
+    if (ndim == 2) {
+        if (maxm <= 1) return launch_fa_rb_batch<2, 1, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+        if (maxm <= 4) return launch_fa_rb_batch<2, 4, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+        if (maxm <= 8) return launch_fa_rb_batch<2, 8, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+        return launch_fa_rb_batch<2, 16, 128, 8, 1>(inst, tile_start, ninst, total_tiles, parity, s);
+    }
+    if (maxm <= 1) return launch_fa_rb_batch<3, 1, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+    if (maxm <= 4) return launch_fa_rb_batch<3, 4, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+    if (maxm <= 8) return launch_fa_rb_batch<3, 8, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
+    return launch_fa_rb_batch<3, 16, 64, 4, 4>(inst, tile_start, ninst, total_tiles, parity, s);
 }
 
 cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,

@@ -901,17 +901,387 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
 
 // ---------------------------------------------------------------- 3D fused kernel ----
 // The 3D counterpart of push_deposit_2d_chunks: per chunk of FUSED_T cell-sorted particles the
-// gather footprint is staged in shared memory ([y][x][z] rows of whole 4-cell groups, one array
-// per component), components are interpolated in pairs with packed FP32 FMAs, and the 3D
-// Esirkepov current
+// gather footprint is staged in shared memory, components are interpolated in pairs with packed
+// FP32 FMAs, and the 3D Esirkepov current
 //   J1(a,b,c) = Cz[a] Txy(b,c), J2(a,b,c) = Cx[b] Tzy(a,c), J3(a,b,c) = Cy[c] Tzx(a,b),
 //   C_d = -(q w/V)(h_d/dt) cumsum dS_d,  T_uv = S0_u (S0_v + dS_v/2) + dS_u (S0_v/2 + dS_v/3)
 // is accumulated in a 32-bit fixed-point box as in 2D (T_uv lies in [0, 1], so |C_d| bounds
 // every contribution).
-constexpr int F_CAP3 = 8192;       // 3D field box floats (6 components)
-constexpr int J_CAP3 = 9216;       // 3D current box ints (3 components)
-constexpr int PF3 = 7;             // prefetched words per particle (cell, 3 offsets, 3 momenta)
-constexpr int SMEM_3D = F_CAP3 + J_CAP3 + 2 * PF3 * FUSED_T;
+//
+// Both shared-memory boxes have compile-time strides, so every interpolation load and every
+// deposit address is a base register plus an immediate, and the staging index arithmetic uses
+// constant divisors.  A chunk of 256 particles sorted in 4 x 4 x 4-cell tiles spans at most three
+// tiles of a uniform 2-per-cell plasma (chunk and tile boundaries do not line up); three tiles
+// along z need at most 17 x 7 x 7 field nodes and 19 x 10 x 10 current nodes.  A chunk whose boxes
+// do not fit (a tile row ends inside it, sparse regions, particles injected since the last sort)
+// takes the global-memory gather and global atomics instead.  The current box is cleared once when the
+// CTA starts and then by the flush that empties it, so a chunk does not clear it again.
+// Rows hold up to 20 z nodes: with a row pitch of 20 words the cells of a sorted warp (4 along z,
+// 4 along x) fall on distinct shared-memory banks for both boxes (a pitch of 16 would put x and
+// x + 2 on the same banks).
+constexpr int FZ3 = 20, FZP3 = 20, FX3 = 8, FY3 = 8;     // field box per component: [y][x][z]
+constexpr int FV3 = FZP3 * FX3 * FY3;
+constexpr int JZ3 = 20, JZP3 = 20, JX3 = 10, JY3 = 10;   // current box per component: [y][x][z]
+constexpr int JV3 = JZP3 * JX3 * JY3;
+constexpr int PF3 = 7;                           // prefetched words per particle (cell, 3 offsets, 3 momenta)
+constexpr int SMEM_3D = 6 * FV3 + 3 * JV3 + 2 * PF3 * FUSED_T;
+static_assert((3 * JV3) % 4 == 0 && FZP3 % 4 == 0 && JZP3 % 4 == 0, "16-byte groups");
+
+// .x = sum Wza Wxa Wya Fa, .y = sum Wzb Wxb Wyb Fb over K^3 nodes of the fixed-stride field box;
+// oa, ob: offsets of the two stencil origins.
+template <int K>
+__device__ __forceinline__ float2 tile_interp3_fixed(const float* __restrict__ Fa, const float (&Wza)[K],
+                                                     const float (&Wxa)[K], const float (&Wya)[K],
+                                                     const float* __restrict__ Fb, const float (&Wzb)[K],
+                                                     const float (&Wxb)[K], const float (&Wyb)[K]) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        float2 tc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < K; ++b) {
+            const float* ra = Fa + (c * FX3 + b) * FZP3;
+            const float* rb = Fb + (c * FX3 + b) * FZP3;
+            float2 t = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < K; ++a) t = __ffma2_rn(make_float2(Wza[a], Wzb[a]), make_float2(ra[a], rb[a]), t);
+            tc = __ffma2_rn(make_float2(Wxa[b], Wxb[b]), t, tc);
+        }
+        acc = __ffma2_rn(make_float2(Wya[c], Wyb[c]), tc, acc);
+    }
+    return acc;
+}
+
+// Global-memory gather and deposition for chunks whose boxes do not fit the shared-memory
+// tiles.  Kept out of line: inlined, their registers would be reserved by the whole kernel.
+template <int SHAPE>
+__device__ __noinline__ void gather3_global(const GridP g, const float* __restrict__ E, const float* __restrict__ B,
+                                            const Pos p0, float* eb) {
+    gather<3, SHAPE>(g, E, B, p0, eb);
+}
+template <int SHAPE>
+__device__ __noinline__ void deposit3_global(const GridP g, float qv, const Pos p0, const Pos p1, float* J) {
+    GlobalAcc acc{&g, J};
+    deposit<3, SHAPE>(g, qv, 0.f, p0, p1, acc);
+}
+
+// DEFER: a chunk whose boxes do not fit is appended to defer[2..] (count in defer[0]) and left for
+// push_deposit_3d_deferred_kernel; otherwise it takes the out-of-line global-memory path here.
+template <int SHAPE, bool DEFER>
+__device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const SpeciesP& sp,
+                                                       const float* __restrict__ E, const float* __restrict__ B,
+                                                       float* __restrict__ J, int shift, long long chunk0,
+                                                       long long stride, float* sF, float* sJ, int* box,
+                                                       int* __restrict__ defer) {
+    constexpr int K = Shape<SHAPE>::K;
+    constexpr int KW = K + 1;
+    const long long n = *sp.count;
+    const long long cap = sp.cap;
+    const int N = (int)g.ncell;
+    const bool fvec = (g.nz & 3) == 0 && aligned16(E) && aligned16(B);
+    const bool jvec = (g.nz & 3) == 0 && aligned16(J);
+    int* const iJ = reinterpret_cast<int*>(sJ);
+    float* const pfb = sJ + 3 * JV3;                  // [2][PF3][FUSED_T]
+    auto prefetch = [&](long long b, int buf) {
+        const long long q = b + threadIdx.x;
+        if (q < n) {
+            float* d = pfb + buf * PF3 * FUSED_T + threadIdx.x;
+            cp_async4(d, sp.cell + q);
+            cp_async4(d + FUSED_T, sp.off + q);
+            cp_async4(d + 2 * FUSED_T, sp.off + cap + q);
+            cp_async4(d + 3 * FUSED_T, sp.off + 2 * cap + q);
+            cp_async4(d + 4 * FUSED_T, sp.u + q);
+            cp_async4(d + 5 * FUSED_T, sp.u + cap + q);
+            cp_async4(d + 6 * FUSED_T, sp.u + 2 * cap + q);
+        }
+        cp_async_commit();
+    };
+    int buf = 0;
+    prefetch(chunk0 * FUSED_T, 0);
+    // box[0..6] and box[7..13] serve alternate chunks: no barrier at the top of the loop or after
+    // the flush.  The current box starts cleared.
+    if (threadIdx.x < 14) {
+        const int q = threadIdx.x % 7;
+        box[threadIdx.x] = q == 6 ? 0 : (q & 1) ? INT_MIN : INT_MAX;
+    }
+    for (int i = threadIdx.x; i < (3 * JV3) / 4; i += FUSED_T)
+        reinterpret_cast<int4*>(iJ)[i] = make_int4(0, 0, 0, 0);
+    __syncthreads();
+    int cur = 0;
+    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T, buf ^= 1, cur ^= 7) {
+        int* const bc = box + cur;
+        if (threadIdx.x < 7) box[(cur ^ 7) + threadIdx.x] = threadIdx.x == 6 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
+        prefetch(base + stride * FUSED_T, buf ^ 1);
+        cp_async_wait_prev();                      // this thread's words of this chunk
+        const long long p = base + threadIdx.x;
+        const float* mine = pfb + buf * PF3 * FUSED_T + threadIdx.x;
+        // ---- load and decode ----
+        bool ok = false;
+        Pos p0;
+        float u[3] = {0.f, 0.f, 0.f};
+        if (p < n) {
+            int cell = __float_as_int(mine[0]);
+            if (cell >= 0) {
+                int izg;
+                decode(g, cell, izg, p0.ix, p0.iy);
+                p0.iz = izg - 1 - shift;
+                if (p0.iz >= 0 && p0.iz < g.nz) {
+                    ok = true;
+                    p0.oz = mine[FUSED_T];
+                    p0.ox = mine[2 * FUSED_T];
+                    p0.oy = mine[3 * FUSED_T];
+                    u[0] = mine[4 * FUSED_T];
+                    u[1] = mine[5 * FUSED_T];
+                    u[2] = mine[6 * FUSED_T];
+                } else {
+                    sp.cell[p] = -1;
+                }
+            }
+        }
+        // ---- gather weights and the chunk's boxes ----
+        float Wzn[K], Wzh[K], Wxn[K], Wxh[K], Wyn[K], Wyh[K];
+        int bzn = 0, bzh = 0, bxn = 0, bxh = 0, byn = 0, byh = 0;
+        if (ok) {
+            bzn = p0.iz + Shape<SHAPE>::w(p0.oz, Wzn);
+            bzh = half_weights<SHAPE>(p0.iz, p0.oz, Wzh);
+            bxn = p0.ix + Shape<SHAPE>::w(p0.ox, Wxn);
+            bxh = half_weights<SHAPE>(p0.ix, p0.ox, Wxh);
+            byn = p0.iy + Shape<SHAPE>::w(p0.oy, Wyn);
+            byh = half_weights<SHAPE>(p0.iy, p0.oy, Wyh);
+        }
+        box_reduce(bc, ok ? min(bzn, bzh) : INT_MAX, ok ? max(bzn, bzh) + K - 1 : INT_MIN,
+                   ok ? min(bxn, bxh) : INT_MAX, ok ? max(bxn, bxh) + K - 1 : INT_MIN);
+        {
+            const int c = __reduce_min_sync(0xffffffffu, ok ? min(byn, byh) : INT_MAX);
+            const int d = __reduce_max_sync(0xffffffffu, ok ? max(byn, byh) + K - 1 : INT_MIN);
+            if ((threadIdx.x & 31) == 0 && c != INT_MAX) {
+                atomicMin(bc + 4, c);
+                atomicMax(bc + 5, d);
+            }
+        }
+        __syncthreads();
+        const bool any = bc[0] != INT_MAX;
+        const int fz0 = bc[0] & ~3, fx0 = bc[2], fy0 = bc[4];
+        const int fzl = bc[1] + 1 - fz0, fxl = bc[3] - bc[2] + 1, fyl = bc[5] - bc[4] + 1;
+        const bool ftile = any && fzl <= FZ3 && fxl <= FX3 && fyl <= FY3;
+        // every deposition window lies within one node below and two above the gather stencils
+        const int jz0 = (bc[0] - 1) & ~3, jx0 = bc[2] - 1, jy0 = bc[4] - 1;
+        const int jzl = bc[1] + 3 - jz0, jxl = bc[3] - bc[2] + 4, jyl = bc[5] - bc[4] + 4;
+        const bool jtile = any && jzl <= JZ3 && jxl <= JX3 && jyl <= JY3;
+        if (DEFER && any && !(ftile && jtile)) {
+            if (threadIdx.x == 0) defer[2 + atomicAdd(defer, 1)] = (int)(base / FUSED_T);
+            __syncthreads();                       // everyone has read this chunk's box words
+            continue;
+        }
+        if (ftile) {
+            // groups (c, y, x, z4) of the [c][y][x][z] box, only those inside the used extents
+#pragma unroll 2
+            for (int i = threadIdx.x; i < 6 * FY3 * FX3 * (FZ3 / 4); i += FUSED_T) {
+                const int zg = i % (FZ3 / 4), r = i / (FZ3 / 4);
+                const int x = r & (FX3 - 1), y = (r >> 3) & (FY3 - 1), c = r >> 6;
+                if (4 * zg >= fzl || x >= fxl || y >= fyl) continue;
+                const long long row = ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
+                const float* f = (c < 3 ? E + c * N : B + (c - 3) * N) + row;
+                *reinterpret_cast<float4*>(sF + c * FV3 + (y * FX3 + x) * FZP3 + 4 * zg) =
+                    load_group(f, fz0 + 4 * zg, g.nz, fvec);
+            }
+        }
+        static_assert(FX3 == 8 && FY3 == 8, "staging index decomposition");
+        __syncthreads();
+        // ---- gather (E1 z+, E2 x+, E3 y+, B1 x+ y+, B2 z+ y+, B3 z+ x+) ----
+        float eb[6];
+        if (ok) {
+            if (ftile) {
+                auto at = [&](int comp, int z, int x, int y) {
+                    return sF + comp * FV3 + ((y - fy0) * FX3 + (x - fx0)) * FZP3 + (z - fz0);
+                };
+                const float2 q1 = tile_interp3_fixed<K>(at(0, bzh, bxn, byn), Wzh, Wxn, Wyn, at(4, bzh, bxn, byh), Wzh,
+                                                        Wxn, Wyh);                            // E1, B2
+                const float2 q2 = tile_interp3_fixed<K>(at(1, bzn, bxh, byn), Wzn, Wxh, Wyn, at(3, bzn, bxh, byh), Wzn,
+                                                        Wxh, Wyh);                            // E2, B1
+                const float2 q3 = tile_interp3_fixed<K>(at(2, bzn, bxn, byh), Wzn, Wxn, Wyh, at(5, bzh, bxh, byn), Wzh,
+                                                        Wxh, Wyn);                            // E3, B3
+                eb[0] = q1.x;
+                eb[4] = q1.y;
+                eb[1] = q2.x;
+                eb[3] = q2.y;
+                eb[2] = q3.x;
+                eb[5] = q3.y;
+            } else if (!DEFER) {
+                gather3_global<SHAPE>(g, E, B, p0, eb);
+            }
+        }
+        // ---- push and move ----
+        Pos p1 = p0;
+        if (ok) {
+            boris(sp.eps, eb, u);
+            float gh, gl, rg;
+            gamma_ff(u, gh, gl, rg);
+            float dzh, dzl, dxh, dxl, dyh, dyl;
+            displacement(u[0], gh, gl, rg, sp.kz[0], sp.kz[1], dzh, dzl);
+            displacement(u[1], gh, gl, rg, sp.kx[0], sp.kx[1], dxh, dxl);
+            displacement(u[2], gh, gl, rg, sp.ky[0], sp.ky[1], dyh, dyl);
+            if (!(fabsf(dzh) < 1.f && fabsf(dxh) < 1.f && fabsf(dyh) < 1.f)) {
+                ok = false;
+                sp.cell[p] = -1;
+            } else {
+                advance_axis(p1.iz, p1.oz, dzh, dzl);
+                advance_axis(p1.ix, p1.ox, dxh, dxl);
+                advance_axis(p1.iy, p1.oy, dyh, dyl);
+                const int wx = wrapi(p1.ix, g.nx), wy = wrapi(p1.iy, g.ny);
+                sp.cell[p] = (p1.iz >= 0 && p1.iz < g.nz) ? encode(g, p1.iz, wx, wy) : -1;
+                sp.off[p] = p1.oz;
+                sp.off[cap + p] = p1.ox;
+                sp.off[2 * cap + p] = p1.oy;
+                sp.u[p] = u[0];
+                sp.u[cap + p] = u[1];
+                sp.u[2 * cap + p] = u[2];
+            }
+        }
+        // ---- deposition ----
+        float S0z[KW], DSz[KW], S0x[KW], DSx[KW], S0y[KW], DSy[KW];
+        int bz = 0, bx = 0, by = 0;
+        if (ok) {
+            bz = axis_weights_from<SHAPE>(bzn, Wzn, p1.iz, p1.oz, S0z, DSz);
+            bx = axis_weights_from<SHAPE>(bxn, Wxn, p1.ix, p1.ox, S0x, DSx);
+            by = axis_weights_from<SHAPE>(byn, Wyn, p1.iy, p1.oy, S0y, DSy);
+        } else {
+#pragma unroll
+            for (int k = 0; k < KW; ++k) S0z[k] = DSz[k] = S0x[k] = DSx[k] = S0y[k] = DSy[k] = 0.f;
+        }
+        const float f1 = -sp.qv * g.dz / g.dt, f2 = -sp.qv * g.dx / g.dt, f3 = -sp.qv * g.dy / g.dt;
+        float cz[KW], cx[KW], cy[KW];
+        float mb = 0.f;
+        {
+            float az = 0.f, ax = 0.f, ay = 0.f;
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                az += DSz[k];
+                ax += DSx[k];
+                ay += DSy[k];
+                cz[k] = az;
+                cx[k] = ax;
+                cy[k] = ay;
+                mb = fmaxf(mb, fmaxf(fabsf(f1 * az), fmaxf(fabsf(f2 * ax), fabsf(f3 * ay))));
+            }
+        }
+        // fixed-point scale of the chunk (see push_deposit_2d_chunks): s = 2^(22-e), max mb < 2^e
+        if (jtile) {
+            const unsigned wm = __reduce_max_sync(0xffffffffu, ok ? __float_as_uint(mb) : 0u);
+            if ((threadIdx.x & 31) == 0 && wm) atomicMax(reinterpret_cast<unsigned*>(bc + 6), wm);
+        }
+        __syncthreads();
+        const int mbits = bc[6];
+        const int sexp = min(275 - (mbits >> 23), 253);
+        const float fs = __int_as_float(sexp << 23), inv_s = __int_as_float((254 - sexp) << 23);
+        if (jtile && mbits != 0) {
+#pragma unroll
+            for (int k = 0; k < KW; ++k) {
+                cz[k] *= f1 * fs;
+                cx[k] *= f2 * fs;
+                cy[k] *= f3 * fs;
+            }
+            // P = S0 + dS/2 and Q = S0/2 + dS/3 of an axis, formed where they are used
+            auto P_ = [](float s0, float ds) { return fmaf(0.5f, ds, s0); };
+            auto Q_ = [](float s0, float ds) { return fmaf(1.f / 3.f, ds, 0.5f * s0); };
+            // window origins are >= -2 and below 2^20 - 4 on every axis: an exact 64-bit key
+            const unsigned long long key =
+                ok ? (((unsigned long long)(bz + 4) << 40) | ((unsigned long long)(bx + 4) << 20) |
+                      (unsigned long long)(by + 4))
+                   : (0xFFFFF00000000000ull | (unsigned)threadIdx.x);
+            // direct atomics when at most 4 lanes share a window (144 deposits per particle make
+            // conflicts costlier than in 2D), else sums over runs of lanes first
+            const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
+            int* s0 = iJ + ((by - jy0) * JX3 + (bx - jx0)) * JZP3 + (bz - jz0);
+            const float MAGIC = 12582912.f;           // 1.5 2^23
+            // one component at a time: fewer values live at once
+            auto terms = [&](auto&& put) {
+#pragma unroll
+                for (int c = 0; c < KW; ++c) {
+                    const float py = P_(S0y[c], DSy[c]), qy = Q_(S0y[c], DSy[c]);
+#pragma unroll
+                    for (int b = 0; b < KW; ++b) {
+                        const float t = fmaf(S0x[b], py, DSx[b] * qy);
+#pragma unroll
+                        for (int a = 0; a < KW - 1; ++a) put((c * JX3 + b) * JZP3 + a, fmaf(cz[a], t, MAGIC));
+                    }
+#pragma unroll
+                    for (int a = 0; a < KW; ++a) {
+                        const float t = fmaf(S0z[a], py, DSz[a] * qy);
+#pragma unroll
+                        for (int b = 0; b < KW - 1; ++b) put(JV3 + (c * JX3 + b) * JZP3 + a, fmaf(cx[b], t, MAGIC));
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < KW; ++b) {
+                    const float px = P_(S0x[b], DSx[b]), qx = Q_(S0x[b], DSx[b]);
+#pragma unroll
+                    for (int a = 0; a < KW; ++a) {
+                        const float t = fmaf(S0z[a], px, DSz[a] * qx);
+#pragma unroll
+                        for (int c = 0; c < KW - 1; ++c)
+                            put(2 * JV3 + (c * JX3 + b) * JZP3 + a, fmaf(cy[c], t, MAGIC));
+                    }
+                }
+            };
+            if (gmax <= 4) {
+                if (ok) terms([&](int o, float biased) { atomicAdd(s0 + o, __float_as_int(biased) - 0x4B400000); });
+            } else {
+                const SegReduce seg = make_segments(key);
+                terms([&](int o, float biased) {
+                    const int v = seg.sum(__float_as_int(biased) - 0x4B400000);
+                    if (seg.head && ok && v != 0) atomicAdd(s0 + o, v);
+                });
+            }
+        } else if (!DEFER && any && !jtile && ok) {
+            deposit3_global<SHAPE>(g, sp.qv, p0, p1, J);
+        }
+        __syncthreads();
+        if (jtile && mbits != 0) {
+            // box -> J in 16-byte groups (one vector atomic per group inside the grid); the groups
+            // are cleared as they are read, for the next chunk
+            const int ng = (jzl + 3) >> 2;
+            for (int i = threadIdx.x; i < 3 * JY3 * JX3 * (JZ3 / 4); i += FUSED_T) {
+                const int zg = i % (JZ3 / 4), r = i / (JZ3 / 4);
+                const int x = r % JX3, rr = r / JX3;
+                const int y = rr % JY3, c = rr / JY3;
+                if (zg >= ng || x >= jxl || y >= jyl) continue;
+                int4* grp = reinterpret_cast<int4*>(iJ + c * JV3 + (y * JX3 + x) * JZP3) + zg;
+                const int4 q = *grp;
+                if ((q.x | q.y | q.z | q.w) == 0) continue;
+                *grp = make_int4(0, 0, 0, 0);
+                const float4 v = make_float4((float)q.x * inv_s, (float)q.y * inv_s, (float)q.z * inv_s,
+                                             (float)q.w * inv_s);
+                const int gz = jz0 + 4 * zg;
+                float* dst = J + c * N + (wrapi(jy0 + y, g.ny) * g.nx + wrapi(jx0 + x, g.nx)) * g.nz + gz;
+                if (jvec && gz >= 0 && gz + 3 < g.nz) {
+                    atomicAdd(reinterpret_cast<float4*>(dst), v);
+                } else {
+                    if ((unsigned)gz < (unsigned)g.nz && q.x) atomicAdd(dst, v.x);
+                    if ((unsigned)(gz + 1) < (unsigned)g.nz && q.y) atomicAdd(dst + 1, v.y);
+                    if ((unsigned)(gz + 2) < (unsigned)g.nz && q.z) atomicAdd(dst + 2, v.z);
+                    if ((unsigned)(gz + 3) < (unsigned)g.nz && q.w) atomicAdd(dst + 3, v.w);
+                }
+            }
+        }
+    }
+    cp_async_wait_all_p();                         // the last (empty) prefetch group
+}
+
+template <int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, 3) push_deposit_3d_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
+                                                                     const float* __restrict__ B, float* __restrict__ J,
+                                                                     int shift, int* __restrict__ defer) {
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    __shared__ int box[14];
+    push_deposit_3d_chunks<SHAPE, true>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + 6 * FV3, box,
+                                        defer);
+}
+
+constexpr int F_CAP3 = 8192;       // general path: field box floats (6 components)
+constexpr int J_CAP3 = 9216;       // general path: current box ints (3 components)
+constexpr int SMEM_3D_GEN = F_CAP3 + J_CAP3 + 2 * PF3 * FUSED_T;
 
 // .x = sum Wza Wxa Wya Fa, .y = sum Wzb Wxb Wyb Fb over K^3 nodes of [y][x][z] boxes (row fzl,
 // fxl rows per plane); (z, x, y) are the stencil origins in the box.
@@ -939,11 +1309,13 @@ __device__ __forceinline__ float2 tile_interp3_pair(const float* __restrict__ Fa
     return acc;
 }
 
+// The general path for the chunks push_deposit_3d_kernel leaves (list[0 .. nlist)): boxes of any
+// shape up to F_CAP3 / J_CAP3 words, runtime strides; larger boxes use global memory.
 template <int SHAPE>
-__device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const SpeciesP& sp,
-                                                       const float* __restrict__ E, const float* __restrict__ B,
-                                                       float* __restrict__ J, int shift, long long chunk0,
-                                                       long long stride, float* sF, float* sJ, int* box) {
+__device__ __forceinline__ void push_deposit_3d_general(const GridP& g, const SpeciesP& sp,
+                                                        const float* __restrict__ E, const float* __restrict__ B,
+                                                        float* __restrict__ J, int shift, const int* __restrict__ list,
+                                                        int nlist, float* sF, float* sJ, int* box) {
     constexpr int K = Shape<SHAPE>::K;
     constexpr int KW = K + 1;
     const long long n = *sp.count;
@@ -967,7 +1339,9 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
         cp_async_commit();
     };
     int buf = 0;
-    prefetch(chunk0 * FUSED_T, 0);
+    const int k0 = blockIdx.x, kst = gridDim.x;
+    auto chunk_base = [&](int k) { return k < nlist ? (long long)list[k] * FUSED_T : n; };
+    prefetch(chunk_base(k0), 0);
     // box[0..6] and box[7..13] serve alternate chunks (see push_deposit_2d_chunks): no barrier at
     // the top of the loop or after the flush
     if (threadIdx.x < 14) {
@@ -976,10 +1350,11 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
     }
     __syncthreads();
     int cur = 0;
-    for (long long base = chunk0 * FUSED_T; base < n; base += stride * FUSED_T, buf ^= 1, cur ^= 7) {
+    for (int k = k0; k < nlist; k += kst, buf ^= 1, cur ^= 7) {
+        const long long base = chunk_base(k);
         int* const bc = box + cur;
         if (threadIdx.x < 7) box[(cur ^ 7) + threadIdx.x] = threadIdx.x == 6 ? 0 : (threadIdx.x & 1) ? INT_MIN : INT_MAX;
-        prefetch(base + stride * FUSED_T, buf ^ 1);
+        prefetch(chunk_base(k + kst), buf ^ 1);
         cp_async_wait_prev();                      // this thread's words of this chunk
         const long long p = base + threadIdx.x;
         const float* mine = pfb + buf * PF3 * FUSED_T + threadIdx.x;
@@ -1223,14 +1598,28 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
     cp_async_wait_all_p();                         // the last (empty) prefetch group
 }
 
+// The chunks push_deposit_3d_kernel deferred (defer[0] of them, chunk indices from defer[2]), on the
+// general path.  The last CTA to finish clears the list (defer[1] counts finished CTAs).
 template <int SHAPE>
-__global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
-                                                                     const float* __restrict__ B, float* __restrict__ J,
-                                                                     int shift) {
+__global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_deferred_kernel(GridP g, SpeciesP sp,
+                                                                              const float* __restrict__ E,
+                                                                              const float* __restrict__ B,
+                                                                              float* __restrict__ J, int shift,
+                                                                              int* __restrict__ defer) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     __shared__ int box[14];
-    push_deposit_3d_chunks<SHAPE>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + F_CAP3, box);
+    const int nd = *(volatile int*)defer;
+    push_deposit_3d_general<SHAPE>(g, sp, E, B, J, shift, defer + 2, nd, smem, smem + F_CAP3, box);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(defer + 1, 1) == (int)gridDim.x - 1) {
+            defer[0] = 0;
+            defer[1] = 0;
+            __threadfence();
+        }
+    }
 }
 
 template <int SHAPE>
@@ -1240,8 +1629,8 @@ __global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_batch_kernel(const
     __shared__ int box[14];
     const PartInst& q = inst[blockIdx.y];
     const GridP g = prep_device(q.g);
-    push_deposit_3d_chunks<SHAPE>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem,
-                                  smem + F_CAP3, box);
+    push_deposit_3d_chunks<SHAPE, false>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem,
+                                         smem + 6 * FV3, box, nullptr);
 }
 
 template <int SHAPE>
@@ -1562,7 +1951,7 @@ inline unsigned pblocks(long long extent) {
 }  // namespace
 
 cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, const float* B, float* J,
-                        int shift, int mode, long long extent, cudaStream_t s) {
+                        int shift, int mode, long long extent, int* defer, cudaStream_t s) {
     const GridP g = prep(g0);
     if (extent <= 0) return cudaSuccess;
     return dispatch(g.ndim, g.shape, [&](auto nd, auto sh) {
@@ -1586,7 +1975,19 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
                 if (e != cudaSuccess) return e;
                 configured = true;
             }
-            k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift);
+            k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift, defer);
+            // the deferred chunks: a fixed grid (their count is on the device)
+            auto kd = push_deposit_3d_deferred_kernel<SH>;
+            const size_t smem_d = SMEM_3D_GEN * sizeof(float);
+            static bool configured_d = false;
+            if (!configured_d) {
+                cudaError_t e = cudaFuncSetAttribute(kd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_d);
+                if (e != cudaSuccess) return e;
+                configured_d = true;
+            }
+            const long long nchunk = (extent + FUSED_T - 1) / FUSED_T;
+            const unsigned nb = (unsigned)(nchunk < 152 * 2 ? (nchunk < 1 ? 1 : nchunk) : 152 * 2);
+            kd<<<nb, FUSED_T, smem_d, s>>>(g, sp, E, B, J, shift, defer);
         } else {
             push_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, shift);
         }

@@ -25,6 +25,7 @@ struct SpeciesSlot {
     double q = 0, m = 1, w = 0;
     int32_t* prev_cell = nullptr;   // library scratch for the unfused path
     float* prev_off = nullptr;
+    int32_t* defer = nullptr;       // 3D fused path: list of chunks left to the global-memory kernel
 };
 
 struct pic_t {
@@ -451,6 +452,7 @@ pic_status pic_destroy(pic_t* h) {
     for (auto& q : h->sp) {
         dfree(q.prev_cell);
         dfree(q.prev_off);
+        dfree(q.defer);
     }
     delete h;
     return PIC_OK;
@@ -494,6 +496,7 @@ pic_status pic_bind_species(pic_t* h, int s, int32_t* cell, float* off, float* u
     SpeciesSlot& sl = h->sp[s];
     dfree(sl.prev_cell);
     dfree(sl.prev_off);
+    dfree(sl.defer);
     sl = SpeciesSlot();
     sl.bound = true;
     sl.cell = cell;
@@ -525,7 +528,7 @@ pic_status pic_gather_push(pic_t* h, void* stream) {
         }
         SpeciesP sp = species_params(h, i);
         Scope sc(h, PIC_T_PARTICLES, 1, s);
-        CK(h, launch_push(h->g, sp, h->E, h->B, nullptr, h->pending_shift, 1, q.extent, s), "push kernel");
+        CK(h, launch_push(h->g, sp, h->E, h->B, nullptr, h->pending_shift, 1, q.extent, nullptr, s), "push kernel");
     }
     h->pending_shift = 0;
     h->state = 1;
@@ -586,9 +589,14 @@ pic_status pic_step(pic_t* h, int nsteps, void* stream) {
         }
         for (int i = 0; i < PIC_MAX_SPECIES; ++i) {
             if (!h->sp[i].bound) continue;
+            SpeciesSlot& q = h->sp[i];
+            if (h->cfg.ndim == 3 && !q.defer) {
+                if ((st = dalloc(h, &q.defer, 2 + (q.cap + 255) / 256, "deferred chunk list"))) return st;
+                CK(h, cudaMemsetAsync(q.defer, 0, sizeof(int32_t) * 2, s), "clear deferred chunk list");
+            }
             SpeciesP sp = species_params(h, i);
-            Scope sc(h, PIC_T_PARTICLES, 1, s);
-            CK(h, launch_push(h->g, sp, Ec, Bc, h->J, h->pending_shift, 0, h->sp[i].extent, s),
+            Scope sc(h, PIC_T_PARTICLES, h->cfg.ndim == 3 ? 2 : 1, s);
+            CK(h, launch_push(h->g, sp, Ec, Bc, h->J, h->pending_shift, 0, q.extent, q.defer, s),
                "fused push/deposit kernel");
         }
         h->pending_shift = 0;
@@ -899,7 +907,10 @@ struct pic_batch_t {
         std::vector<int> members;
         FieldP* d_inst = nullptr;
         int* d_tiles = nullptr;
-        int total = 0, maxm = 1;
+        int4* d_work = nullptr;      // 2D: x-marching work items (instance, z0, first row, end row)
+        int total = 0, maxm = 1, nwork = 0;
+        int variant = 1;             // 0: one cell per thread, 1: register-blocked, 2: x-marching (2D)
+        double ms[3] = {0, 0, 0};    // batch autotune: time of one launch per variant (0: not timed)
     } fg[4];
     struct PartGroup {
         std::vector<int> members;
@@ -980,8 +991,11 @@ pic_status batch_build(pic_batch_t* b) {
         auto& f = b->fg[c];
         std::vector<FieldP> inst;
         std::vector<int> tiles(1, 0);
-        for (int i : f.members) {
-            pic_t* h = b->h[i];
+        std::vector<int4> work;
+        for (int j = 0; j < (int)f.members.size(); ++j) {
+            pic_t* h = b->h[f.members[j]];
+            const bool aligned = ((uintptr_t)h->E | (uintptr_t)h->B | (uintptr_t)h->J | (uintptr_t)h->E2 |
+                                  (uintptr_t)h->B2) % 16 == 0;
             for (int par = 0; par < 2; ++par) {
                 FieldP p;
                 p.g = h->g;
@@ -994,13 +1008,20 @@ pic_status batch_build(pic_batch_t* b) {
                 p.Eout = par ? h->E : h->E2;
                 p.Bout = par ? h->B : h->B2;
                 p.shift = 0;
+                p.vec4 = (h->g.nz % 4 == 0 && aligned) ? 1 : 0;
                 inst.push_back(p);
             }
             tiles.push_back(tiles.back() + field_tiles(b->ndim, maxm_of[c], h->g.nz, h->g.nx, h->g.ny));
+            if (b->ndim == 2)
+                for (int z0 = 0; z0 < h->g.nz; z0 += MARCH2_BATCH_TZ)
+                    for (int xa = 0; xa < h->g.nx; xa += MARCH2_BATCH_XC)
+                        work.push_back(make_int4(j, z0, xa, std::min(xa + MARCH2_BATCH_XC, h->g.nx)));
         }
         f.total = tiles.back();
         f.maxm = maxm_of[c];
-        if (upload(&f.d_inst, inst) != cudaSuccess || upload(&f.d_tiles, tiles) != cudaSuccess)
+        f.nwork = (int)work.size();
+        if (upload(&f.d_inst, inst) != cudaSuccess || upload(&f.d_tiles, tiles) != cudaSuccess ||
+            upload(&f.d_work, work) != cudaSuccess)
             return bfail(b, PIC_ERR_OOM, "batch field tables");
     }
     for (int sh = 0; sh < 2; ++sh) {
@@ -1032,6 +1053,53 @@ pic_status batch_build(pic_batch_t* b) {
     return PIC_OK;
 }
 
+cudaError_t batch_field_launch(pic_batch_t* b, const pic_batch_t::FieldGroup& f, int variant, int parity,
+                               cudaStream_t s) {
+    const int n = (int)f.members.size();
+    if (variant == 2 && b->ndim == 2)
+        return launch_field_advance_march2_batch(f.d_inst, f.d_work, f.nwork, f.maxm, parity, s);
+    if (variant == 1) return launch_field_advance_rb_batch(f.d_inst, f.d_tiles, n, f.total, b->ndim, f.maxm, parity, s);
+    return launch_field_advance_batch(f.d_inst, f.d_tiles, n, f.total, b->ndim, f.maxm, parity, s);
+}
+
+// Batch autotune: per stencil class, time one field-advance launch (parity 0: reads E, B, J,
+// writes the second buffers, which the step overwrites) with each variant and keep the fastest.
+pic_status batch_autotune(pic_batch_t* b, cudaStream_t s) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return bfail(b, PIC_ERR_CUDA, "batch autotune events");
+    pic_status st = PIC_OK;
+    for (auto& f : b->fg) {
+        if (f.members.empty()) continue;
+        const int nv = b->ndim == 2 ? 3 : 2;
+        double best = 1e30;
+        for (int v = 0; v < nv && st == PIC_OK; ++v) {
+            cudaError_t e = batch_field_launch(b, f, v, 0, s);            // warm-up
+            float ms = 0.f, tot = 0.f;
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) {
+                e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) e = batch_field_launch(b, f, v, 0, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                tot += ms;
+            }
+            if (e != cudaSuccess) {
+                st = bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
+                break;
+            }
+            f.ms[v] = tot / 3.0;
+            if (f.ms[v] < best) {
+                best = f.ms[v];
+                f.variant = v;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
 // one step of every instance, reading the field buffers of this parity
 cudaError_t batch_enqueue_step(pic_batch_t* b, int parity, cudaStream_t s) {
     cudaError_t e;
@@ -1043,11 +1111,10 @@ cudaError_t batch_enqueue_step(pic_batch_t* b, int parity, cudaStream_t s) {
             return e;
     if (b->nfilt && (e = launch_filter_current_batch(b->d_filt, b->nfilt, b->max_rows3, s))) return e;
     if (b->ncorr && (e = launch_correct_j1_batch(b->d_corr, b->ncorr, b->max_rows, b->max_nz, s))) return e;
-    for (auto& f : b->fg)
-        if (!f.members.empty() &&
-            (e = launch_field_advance_batch(f.d_inst, f.d_tiles, (int)f.members.size(), f.total, b->ndim, f.maxm,
-                                            parity, s)))
-            return e;
+    for (auto& f : b->fg) {
+        if (f.members.empty()) continue;
+        if ((e = batch_field_launch(b, f, f.variant, parity, s))) return e;
+    }
     return cudaSuccess;
 }
 
@@ -1101,6 +1168,7 @@ pic_status pic_batch_step(pic_batch_t* b, int nsteps, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     if (!b->built) {
         pic_status st = batch_build(b);
+        if (!st) st = batch_autotune(b, s);
         if (st) return st;
     }
     if (!b->graph) {
@@ -1134,6 +1202,16 @@ pic_status pic_batch_step(pic_batch_t* b, int nsteps, void* stream) {
     return PIC_OK;
 }
 
+pic_status pic_batch_get_tuning(const pic_batch_t* b, int* variant, double* ms) {
+    if (!b) return PIC_ERR_ARG;
+    for (int c = 0; c < 4; ++c) {
+        if (variant) variant[c] = b->fg[c].members.empty() ? -1 : b->fg[c].variant;
+        if (ms)
+            for (int v = 0; v < 3; ++v) ms[3 * c + v] = b->fg[c].ms[v];
+    }
+    return PIC_OK;
+}
+
 pic_status pic_batch_destroy(pic_batch_t* b) {
     if (!b) return PIC_OK;
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -1141,6 +1219,7 @@ pic_status pic_batch_destroy(pic_batch_t* b) {
     for (auto& f : b->fg) {
         dfree(f.d_inst);
         dfree(f.d_tiles);
+        dfree(f.d_work);
     }
     for (auto& q : b->pg) dfree(q.d_inst);
     dfree(b->d_corr);

@@ -113,12 +113,23 @@ int default_field_variant(int ndim, int M);
 cudaError_t launch_field_advance_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,
                                        int ndim, int maxm, int parity, cudaStream_t s);
 int field_tiles(int ndim, int maxm, int nz, int nx, int ny);
+// Batched 2D field advance with the x-marching segments: work[w] = (instance, z0, first row,
+// last row + 1); z segments of MARCH2_BATCH_TZ cells.
+constexpr int MARCH2_BATCH_TZ = 192;
+constexpr int MARCH2_BATCH_XC = 32;
+// The same tile list as launch_field_advance_batch with register-blocked tiles.
+cudaError_t launch_field_advance_rb_batch(const FieldP* inst, const int* tile_start, int ninst, int total_tiles,
+                                          int ndim, int maxm, int parity, cudaStream_t s);
+cudaError_t launch_field_advance_march2_batch(const FieldP* inst, const int4* work, int nwork, int maxm, int parity,
+                                              cudaStream_t s);
 cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_rows, int max_nz, cudaStream_t s);
 cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int shape, long long max_extent, int parity,
                               cudaStream_t s);
 cudaError_t launch_zero_j_batch(const PartInst* inst, int ninst, long long max_ncell, cudaStream_t s);
+// defer (3D fused mode): library scratch of 2 + ceil(cap / 256) ints, zero on first use: the
+// chunks whose shared-memory boxes do not fit, processed by a second kernel that clears the list.
 cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, const float* B,
-                        float* J, int shift, int mode, long long extent, cudaStream_t s);
+                        float* J, int shift, int mode, long long extent, int* defer, cudaStream_t s);
 cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J, long long extent,
                                    cudaStream_t s);
 cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], long long next_id,

@@ -215,3 +215,29 @@ def beam_plasma_3d_sample(frac, seed=7):
     beam = species(beam["iz"][keep], beam["ix"][keep], beam["iy"][keep], beam["off"][:, keep], beam["u"][:, keep],
                    beam["q"], beam["m"], beam["w"])
     return grid, [plasma, beam], n_plasma + 4_000_000
+
+
+# customised-stencil stability fixed point at r = 1: kappa = dz/dt at which dt equals the limit
+# of the stencil fitted at that same kappa (Appendix C fit)
+KAPPA_CFL_CUSTOM_2D = 1.632488686516034
+
+
+def batched_vacuum_scan(n=256, seed=4000):
+    """Instance parameters of the batched vacuum scan: n independent 2D single-particle runs with
+    nz ~ U{128..1024}, nx ~ U{64..256}, log10 gamma ~ U[1, 5], dt = U[0.3, 0.99] x the instance's
+    own stability limit, Yee or customised (M = 16) by a fair coin, dz = dx = 0.05, linear shape.
+    Returns [(grid dict, gamma)]."""
+    rng = np.random.default_rng(seed)
+    d = 0.05
+    out = []
+    for _ in range(n):
+        nz = int(rng.integers(128, 1025))
+        nx = int(rng.integers(64, 257))
+        gamma = 10 ** rng.uniform(1, 5)
+        frac = rng.uniform(0.3, 0.99)
+        custom = bool(rng.integers(0, 2))
+        dt = frac * (d / KAPPA_CFL_CUSTOM_2D if custom else d / math.sqrt(2))
+        grid = dict(ndim=2, nz=nz, nx=nx, ny=1, dz=d, dx=d, dy=d, dt=dt, shape=1,
+                    solver="custom" if custom else "yee", M=16)
+        out.append((grid, gamma))
+    return out
