@@ -912,16 +912,16 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
 // deposit address is a base register plus an immediate, and the staging index arithmetic uses
 // constant divisors.  A chunk of 256 particles sorted in 4 x 4 x 4-cell tiles spans at most three
 // tiles of a uniform 2-per-cell plasma (chunk and tile boundaries do not line up); three tiles
-// along z need at most 17 x 7 x 7 field nodes and 19 x 10 x 10 current nodes.  A chunk whose boxes
-// do not fit (a tile row ends inside it, sparse regions, particles injected since the last sort)
-// takes the global-memory gather and global atomics instead.  The current box is cleared once when the
+// along z, whatever their alignment to the 4-cell groups after window shifts, need at most 18 x 7 x 7
+// field nodes and 21 x 10 x 10 current nodes.  A chunk whose boxes do not fit (a tile row ends
+// inside it, sparse regions, particles injected since the last sort) takes the general path.  The current box is cleared once when the
 // CTA starts and then by the flush that empties it, so a chunk does not clear it again.
-// Rows hold up to 20 z nodes: with a row pitch of 20 words the cells of a sorted warp (4 along z,
-// 4 along x) fall on distinct shared-memory banks for both boxes (a pitch of 16 would put x and
-// x + 2 on the same banks).
+// Field rows hold up to 20 z nodes, current rows up to 24: with row pitches of 20 and 24 words the
+// cells of a sorted warp (4 along z, 4 along x) fall on distinct shared-memory banks (a pitch of
+// 16 would put x and x + 2 on the same banks).
 constexpr int FZ3 = 20, FZP3 = 20, FX3 = 8, FY3 = 8;     // field box per component: [y][x][z]
 constexpr int FV3 = FZP3 * FX3 * FY3;
-constexpr int JZ3 = 20, JZP3 = 20, JX3 = 10, JY3 = 10;   // current box per component: [y][x][z]
+constexpr int JZ3 = 24, JZP3 = 24, JX3 = 10, JY3 = 10;   // current box per component: [y][x][z]
 constexpr int JV3 = JZP3 * JX3 * JY3;
 constexpr int PF3 = 7;                           // prefetched words per particle (cell, 3 offsets, 3 momenta)
 constexpr int SMEM_3D = 6 * FV3 + 3 * JV3 + 2 * PF3 * FUSED_T;
@@ -1073,6 +1073,7 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
             __syncthreads();                       // everyone has read this chunk's box words
             continue;
         }
+        unsigned fbits = 0u;                       // any nonzero bit among the staged field values
         if (ftile) {
             // groups (c, y, x, z4) of the [c][y][x][z] box, only those inside the used extents
 #pragma unroll 2
@@ -1082,12 +1083,21 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
                 if (4 * zg >= fzl || x >= fxl || y >= fyl) continue;
                 const long long row = ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
                 const float* f = (c < 3 ? E + c * N : B + (c - 3) * N) + row;
-                *reinterpret_cast<float4*>(sF + c * FV3 + (y * FX3 + x) * FZP3 + 4 * zg) =
-                    load_group(f, fz0 + 4 * zg, g.nz, fvec);
+                const float4 v = load_group(f, fz0 + 4 * zg, g.nz, fvec);
+                fbits |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+                *reinterpret_cast<float4*>(sF + c * FV3 + (y * FX3 + x) * FZP3 + 4 * zg) = v;
             }
         }
         static_assert(FX3 == 8 && FY3 == 8, "staging index decomposition");
-        __syncthreads();
+        // a particle at rest in zero fields stays at rest and carries no current
+        const bool moving = ok && (u[0] != 0.f || u[1] != 0.f || u[2] != 0.f);
+        if (!__syncthreads_or(fbits != 0u || moving) && ftile) {
+            // a quiet chunk (every particle at rest, every field of its footprint zero): nothing
+            // moves and no current flows; only a pending window shift is applied to the cells,
+            // and the rest of the chunk runs with every particle switched off
+            if (shift && ok) sp.cell[p] = encode(g, p0.iz, p0.ix, p0.iy);
+            ok = false;
+        }
         // ---- gather (E1 z+, E2 x+, E3 y+, B1 x+ y+, B2 z+ y+, B3 z+ x+) ----
         float eb[6];
         if (ok) {
