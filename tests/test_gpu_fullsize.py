@@ -1,4 +1,5 @@
-"""Parity at full size, in the launch configuration bench.py times (fused pic_step).
+"""Parity at full size, in the launch configuration bench.py times (particles sorted by cell at step 0,
+fused pic_step).
 
 Cases: the 2D beam-in-plasma run (2048 x 512, 5.19M particles, customised M = 16, quadratic)
 and the 3D run (512 x 256 x 256, 71M particles).  One step from seeded random fields; the
@@ -55,7 +56,8 @@ def test_fullsize_step_sampled(case):
     grid, sps = CASES[case]()
     nd, nz, nx, ny = grid["ndim"], grid["nz"], grid["nx"], grid.get("ny", 1)
     C = fit.fit_coefficients(grid["dz"] / grid["dt"])
-    sim = gpu_sim(grid, sps, coef=C, cap_extra=100_000)
+    # sorted by cell before the step, as bench.py runs it (sort_every = 20 sorts at step 0)
+    sim = gpu_sim(grid, sps, coef=C, cap_extra=100_000, sort_every=20)
     rng = np.random.default_rng(77)
     E0, B0 = _random_fields(sim, rng, 0.5)
     G0 = sim.gauss()
@@ -73,10 +75,17 @@ def test_fullsize_step_sampled(case):
     E64, B64 = E0.astype(np.float64), B0.astype(np.float64)
     h = fit.correction_kernel(C, hlen=40)
 
-    # sampled particles (ids are the slot numbers: no sort, no deaths in one step at the centre)
+    # sampled particles, found by id (the sort moved them; no deaths in one step at the centre)
     for s, sp in enumerate(sps):
         n = len(sp["iz"])
         idx = np.sort(rng.choice(n, size=min(400, n), replace=False))
+        ngpu = sim.count(s)
+        gid = sim.species[s]["id"][:ngpu].cpu().numpy().astype(np.int64)
+        slot_of = np.full(n, -1, np.int64)
+        ok_id = (gid >= 0) & (gid < n)
+        slot_of[gid[ok_id]] = np.arange(ngpu)[ok_id]
+        slots = slot_of[idx]
+        assert np.all(slots >= 0)
         xi0 = wl.xi_of({k: (v[..., idx] if isinstance(v, np.ndarray) and v.shape[-1] == n else v)
                         for k, v in sp.items()}, nd)
         u = sp["u"][:, idx].T.astype(np.float64).copy()
@@ -84,9 +93,10 @@ def test_fullsize_step_sampled(case):
         oc.boris(eb, u, sp["q"] * g.dt / (2 * sp["m"]))
         xi1 = oc.move(g, xi0, u)
         d = sim.species[s]
-        cell = d["cell"][idx].cpu().numpy()
-        off = d["off"][:, idx].cpu().numpy().astype(np.float64)
-        ug = d["u"][:, idx].cpu().numpy().T.astype(np.float64)
+        ts = torch.from_numpy(slots).to(d["cell"].device)
+        cell = d["cell"][ts].cpu().numpy()
+        off = d["off"][:, ts].cpu().numpy().astype(np.float64)
+        ug = d["u"][:, ts].cpu().numpy().T.astype(np.float64)
         live = cell >= 0
         assert live.mean() > 0.99
         iz, ix, iy = decode_cells(cell[live], nz, nx)
