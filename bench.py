@@ -584,6 +584,21 @@ def run_ours(args, rank, world, local_rank):
     kms, klaunch, kcount = kernel_breakdown(sim, args.steps)
     barrier()
     ms_max, total_pushes, value = aggregate(ms, count, args.steps, world, dev)
+    developed = None
+    if world == 1 and not args.no_secondary and not args.small and args.workload == "beam3d":
+        # the same run later, in the developed wake (step 400 of the configured 500)
+        done = sim.state()[0]
+        if done < 400:
+            sim.step(400 - done)
+        torch.cuda.synchronize(dev)
+        ms_d, count_d = timed_passes(sim, args.steps, 3, barrier, dev)
+        kms_d, _, kcount_d = kernel_breakdown(sim, args.steps)
+        med_d = float(np.median(ms_d))
+        ach_d = bpp * kcount_d * args.steps / (kms_d["particles"] / 1e3) / 1e9
+        developed = {"steps_from": 400, "pushes_per_s": count_d * args.steps / (med_d / 1e3),
+                     "ms_per_step": med_d / args.steps,
+                     "kernel_ms_per_step": {k: v / args.steps for k, v in kms_d.items()},
+                     "particle_kernel_frac": ach_d / measured_peak()[0]}
     cells = grid["nz"] * grid["nx"] * grid.get("ny", 1)
     cell_rate = cells * args.steps * world / (ms_max / 1e3)
 
@@ -651,6 +666,8 @@ def run_ours(args, rank, world, local_rank):
                  "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
                  "kernel_launches_per_step": {k: v / args.steps for k, v in klaunch.items()},
                  "gauss_change_interior_max": dG, "rho_max": rho_max}
+    if developed:
+        secondary["beam_plasma_3d_developed_wake"] = developed
     cpu = None
     if world == 1 and not args.no_secondary and args.workload == "beam3d" and not args.small:
         secondary["beam_plasma_2d"] = run_beam_secondary(args, dev, "beam2d")

@@ -310,8 +310,9 @@ pic_status pic_set_tuning(pic_t* h, int variant);
  * A batch holds n independent 2D or 3D runs (no moving window, no sort), each with its own
  * grid, dt, stencil (Yee or customised, own coefficients), shape and one particle species.
  * pic_batch_step advances all of them with one launch per kernel class and step (J zero,
- * gather/push/deposit, filter, correction, field advance per stencil class), recorded once into a
- * CUDA graph (two steps, one per field-buffer parity) and replayed on the caller's stream.  The
+ * gather/push/deposit, filter, correction, field advance per stencil class), recorded once into
+ * CUDA graphs (32 steps, replayed while at least 32 remain, and two steps, one per field-buffer
+ * parity) and replayed on the caller's stream.  The
  * field advance of a stencil class walks one work list over all its instances' tiles; the first
  * pic_batch_step after binding times the batched tile variants (one cell per thread, register-
  * blocked, and in 2D x-marching z segments) on the bound fields and keeps the fastest per class

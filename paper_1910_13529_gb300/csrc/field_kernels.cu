@@ -13,6 +13,8 @@
 // buffer lets the moving-window shift be folded into the store.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <cstdint>
 
 #include "pic_internal.h"
@@ -1246,6 +1248,25 @@ cudaError_t launch_fa_rb(const FieldP& p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Rows (2D) or planes (3D) per marching chunk: the chunk count that minimises the number of waves
+// times the rows a CTA walks (its chunk plus the two its prologue recomputes), chunks of at least
+// `minc` rows.  `cols` CTAs march side by side; `slots` CTAs run at once.
+inline int march_chunk(int n, int cols, int slots, int minc) {
+    int best = n, best_cost = INT_MAX;
+    for (int chunks = 1; chunks <= 64; ++chunks) {
+        int c = (n + chunks - 1) / chunks;
+        if (c < minc) c = minc;
+        const long long ctas = (long long)cols * ((n + c - 1) / c);
+        const long long waves = (ctas + slots - 1) / slots;
+        const long long cost = waves * (c + 2);
+        if (cost < best_cost) {
+            best_cost = (int)cost;
+            best = c;
+        }
+    }
+    return best;
+}
+
 template <int MAXM, int TZ, int TX, int NT>
 cudaError_t launch_fa_march(const FieldP& p, cudaStream_t s) {
     using T = MarchT<MAXM, TZ, TX>;
@@ -1261,12 +1282,9 @@ cudaError_t launch_fa_march(const FieldP& p, cudaStream_t s) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int cols = ((p.g.nz + TZ - 1) / TZ) * ((p.g.nx + TX - 1) / TX);
-    const int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
-    const long long want = 4LL * nsm * (per_sm > 0 ? per_sm : 1);
-    int chunks = (int)((want + cols - 1) / cols);
-    chunks = chunks < 1 ? 1 : chunks;
-    int yc = (p.g.ny + chunks - 1) / chunks;
-    yc = yc < 8 ? 8 : yc;
+    int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2048 / NT ? 2048 / NT : per_sm);
+    const int yc = march_chunk(p.g.ny, cols, nsm * per_sm, 8);
     dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, (p.g.ny + yc - 1) / yc);
     k<<<grid, NT, T::smem_bytes, s>>>(p, yc);
     return cudaGetLastError();
@@ -1290,10 +1308,7 @@ cudaError_t launch_fa_march2(const FieldP& p, cudaStream_t s) {
     const int cols = (p.g.nz + TZ - 1) / TZ;
     int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
     per_sm = per_sm < 1 ? 1 : (per_sm > 2048 / NT ? 2048 / NT : per_sm);
-    int chunks = (int)(((long long)nsm * per_sm + cols - 1) / cols);
-    chunks = chunks < 1 ? 1 : chunks;
-    int xc = (p.g.nx + chunks - 1) / chunks;
-    xc = xc < 16 ? 16 : xc;
+    const int xc = march_chunk(p.g.nx, cols, nsm * per_sm, 16);
     dim3 grid(cols, (p.g.nx + xc - 1) / xc, 1);
     k<<<grid, NT, T::smem_bytes, s>>>(p, xc);
     return cudaGetLastError();
@@ -1316,10 +1331,7 @@ cudaError_t launch_fa_march_ring(const FieldP& p, cudaStream_t s) {
     const int cols = ((p.g.nz + TZ - 1) / TZ) * ((p.g.nx + TX - 1) / TX);
     int per_sm = (int)((227 * 1024) / (T::smem_bytes + 1024));
     per_sm = per_sm < 1 ? 1 : (per_sm > 2048 / NT ? 2048 / NT : per_sm);
-    int chunks = (int)(((long long)nsm * per_sm + cols - 1) / cols);
-    chunks = chunks < 1 ? 1 : chunks;
-    int yc = (p.g.ny + chunks - 1) / chunks;
-    yc = yc < 8 ? 8 : yc;
+    const int yc = march_chunk(p.g.ny, cols, nsm * per_sm, 8);
     dim3 grid((p.g.nz + TZ - 1) / TZ, (p.g.nx + TX - 1) / TX, (p.g.ny + yc - 1) / yc);
     k<<<grid, NT, T::smem_bytes, s>>>(p, yc);
     return cudaGetLastError();

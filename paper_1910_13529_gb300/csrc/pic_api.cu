@@ -926,7 +926,8 @@ struct pic_batch_t {
     int ndim = 2;
     bool built = false;
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;       // two steps (one per field-buffer parity)
+    cudaGraphExec_t graph_long = nullptr;  // kLongSteps steps, replayed while that many remain
     char err[256] = {0};
 };
 
@@ -1155,10 +1156,14 @@ pic_status pic_batch_create(const pic_config* cfgs, int n, pic_batch_t** out) {
 pic_status pic_batch_instance(pic_batch_t* b, int i, pic_t** h) {
     if (!b || !h || i < 0 || i >= (int)b->h.size()) return PIC_ERR_ARG;
     *h = b->h[i];
-    b->built = false;            // bindings may change: rebuild tables and graph at the next step
+    b->built = false;            // bindings may change: rebuild tables and graphs at the next step
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
+    }
+    if (b->graph_long) {
+        cudaGraphExecDestroy(b->graph_long);
+        b->graph_long = nullptr;
     }
     return PIC_OK;
 }
@@ -1171,20 +1176,37 @@ pic_status pic_batch_step(pic_batch_t* b, int nsteps, void* stream) {
         if (!st) st = batch_autotune(b, s);
         if (st) return st;
     }
-    if (!b->graph) {
+    // record `steps` (even) steps of every instance into one executable graph
+    auto capture = [&](int steps, cudaGraphExec_t* out) -> cudaError_t {
         cudaGraph_t g = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            cudaError_t e1 = batch_enqueue_step(b, 0, b->cap);
-            cudaError_t e2 = batch_enqueue_step(b, 1, b->cap);
+            cudaError_t ek = cudaSuccess;
+            for (int k = 0; k < steps && ek == cudaSuccess; ++k) ek = batch_enqueue_step(b, k & 1, b->cap);
             e = cudaStreamEndCapture(b->cap, &g);
-            if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2;
+            if (e == cudaSuccess) e = ek;
         }
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
         if (g) cudaGraphDestroy(g);
+        return e;
+    };
+    if (!b->graph) {
+        cudaError_t e = capture(2, &b->graph);
         if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
     }
-    for (int k = 0; k + 1 < nsteps; k += 2) {
+    constexpr int kLongSteps = 32;
+    int k = 0;
+    if (nsteps >= kLongSteps) {
+        if (!b->graph_long) {
+            cudaError_t e = capture(kLongSteps, &b->graph_long);
+            if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
+        }
+        for (; k + kLongSteps <= nsteps; k += kLongSteps) {
+            cudaError_t e = cudaGraphLaunch(b->graph_long, s);
+            if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    for (; k + 1 < nsteps; k += 2) {
         cudaError_t e = cudaGraphLaunch(b->graph, s);
         if (e != cudaSuccess) return bfail(b, PIC_ERR_CUDA, cudaGetErrorString(e));
     }
@@ -1215,6 +1237,7 @@ pic_status pic_batch_get_tuning(const pic_batch_t* b, int* variant, double* ms) 
 pic_status pic_batch_destroy(pic_batch_t* b) {
     if (!b) return PIC_OK;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->graph_long) cudaGraphExecDestroy(b->graph_long);
     if (b->cap) cudaStreamDestroy(b->cap);
     for (auto& f : b->fg) {
         dfree(f.d_inst);
