@@ -825,22 +825,34 @@ __device__ __forceinline__ void push_deposit_2d_chunks(const GridP& g, const Spe
             const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
             int* s0 = iJ + (bx - jx0) * jzl + (bz - jz0);
             const float MAGIC = 12582912.f;           // 1.5 2^23
+            // no lane of the warp changed its support node along an axis: the last window node along
+            // it has S0 = dS = 0 and the last cumulative sum along it is zero; skip those deposits
+            const bool uz = __any_sync(0xffffffffu, S0z[KW - 1] != 0.f || DSz[KW - 1] != 0.f);
+            const bool ux = __any_sync(0xffffffffu, S0x[KW - 1] != 0.f || DSx[KW - 1] != 0.f);
             auto terms = [&](auto&& put) {
 #pragma unroll
                 for (int b = 0; b < KW; ++b)
 #pragma unroll
                     for (int a = 0; a < KW; ++a) {
+                        // J1 (a < KW-1): zero at the last cumulative z sum or the last x node;
+                        // J2 (b < KW-1): at the last cumulative x sum or the last z node;
+                        // J3: at the last z node or the last x node
+                        const bool k1 = !((a == KW - 2 && !uz) || (b == KW - 1 && !ux));
+                        const bool k2 = !((b == KW - 2 && !ux) || (a == KW - 1 && !uz));
+                        const bool k3 = !((a == KW - 1 && !uz) || (b == KW - 1 && !ux));
                         const int o = b * jzl + a;
                         if (a < KW - 1 && b < KW - 1) {
-                            const float2 v = __ffma2_rn(CT[a], TC[b], make_float2(MAGIC, MAGIC));
-                            put(o, v.x);
-                            put(jvol + o, v.y);
+                            if (k1 || k2) {
+                                const float2 v = __ffma2_rn(CT[a], TC[b], make_float2(MAGIC, MAGIC));
+                                if (k1) put(o, v.x);
+                                if (k2) put(jvol + o, v.y);
+                            }
                         } else if (a < KW - 1) {
-                            put(o, fmaf(CT[a].x, TC[b].x, MAGIC));
+                            if (k1) put(o, fmaf(CT[a].x, TC[b].x, MAGIC));
                         } else if (b < KW - 1) {
-                            put(jvol + o, fmaf(CT[a].y, TC[b].y, MAGIC));
+                            if (k2) put(jvol + o, fmaf(CT[a].y, TC[b].y, MAGIC));
                         }
-                        put(2 * jvol + o, fmaf(S0z[a], Ax[b], fmaf(DSz[a], Bx[b], MAGIC)));
+                        if (k3) put(2 * jvol + o, fmaf(S0z[a], Ax[b], fmaf(DSz[a], Bx[b], MAGIC)));
                     }
             };
             if (gmax <= 8) {
@@ -1204,33 +1216,53 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
             const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
             int* s0 = iJ + ((by - jy0) * JX3 + (bx - jx0)) * JZP3 + (bz - jz0);
             const float MAGIC = 12582912.f;           // 1.5 2^23
+            // When no lane of the warp changes its support node along an axis, the last node of the
+            // window along that axis has S0 = dS = 0: every product with it is zero, and so is the
+            // last cumulative sum along that axis (the dS sum to zero).  Those deposits are skipped
+            // for the whole warp (the skipped values are exactly zero).
+            const bool uz = __any_sync(0xffffffffu, S0z[KW - 1] != 0.f || DSz[KW - 1] != 0.f);
+            const bool ux = __any_sync(0xffffffffu, S0x[KW - 1] != 0.f || DSx[KW - 1] != 0.f);
+            const bool uy = __any_sync(0xffffffffu, S0y[KW - 1] != 0.f || DSy[KW - 1] != 0.f);
             // one component at a time: fewer values live at once
             auto terms = [&](auto&& put) {
 #pragma unroll
                 for (int c = 0; c < KW; ++c) {
+                    if (c == KW - 1 && !uy) continue;
                     const float py = P_(S0y[c], DSy[c]), qy = Q_(S0y[c], DSy[c]);
 #pragma unroll
                     for (int b = 0; b < KW; ++b) {
+                        if (b == KW - 1 && !ux) continue;
                         const float t = fmaf(S0x[b], py, DSx[b] * qy);
 #pragma unroll
-                        for (int a = 0; a < KW - 1; ++a) put((c * JX3 + b) * JZP3 + a, fmaf(cz[a], t, MAGIC));
+                        for (int a = 0; a < KW - 1; ++a) {
+                            if (a == KW - 2 && !uz) continue;
+                            put((c * JX3 + b) * JZP3 + a, fmaf(cz[a], t, MAGIC));
+                        }
                     }
 #pragma unroll
                     for (int a = 0; a < KW; ++a) {
+                        if (a == KW - 1 && !uz) continue;
                         const float t = fmaf(S0z[a], py, DSz[a] * qy);
 #pragma unroll
-                        for (int b = 0; b < KW - 1; ++b) put(JV3 + (c * JX3 + b) * JZP3 + a, fmaf(cx[b], t, MAGIC));
+                        for (int b = 0; b < KW - 1; ++b) {
+                            if (b == KW - 2 && !ux) continue;
+                            put(JV3 + (c * JX3 + b) * JZP3 + a, fmaf(cx[b], t, MAGIC));
+                        }
                     }
                 }
 #pragma unroll
                 for (int b = 0; b < KW; ++b) {
+                    if (b == KW - 1 && !ux) continue;
                     const float px = P_(S0x[b], DSx[b]), qx = Q_(S0x[b], DSx[b]);
 #pragma unroll
                     for (int a = 0; a < KW; ++a) {
+                        if (a == KW - 1 && !uz) continue;
                         const float t = fmaf(S0z[a], px, DSz[a] * qx);
 #pragma unroll
-                        for (int c = 0; c < KW - 1; ++c)
+                        for (int c = 0; c < KW - 1; ++c) {
+                            if (c == KW - 2 && !uy) continue;
                             put(2 * JV3 + (c * JX3 + b) * JZP3 + a, fmaf(cy[c], t, MAGIC));
+                        }
                     }
                 }
             };
