@@ -157,9 +157,10 @@ static_assert(kHL % 4 == 0, "s + kHL must be 16-byte aligned for the float4 filt
 // floats of the correction's shared row: s[k] = J1[k - kHL] for k < nz4 + kNWIN
 __host__ __device__ constexpr int corr_floats(int nz) { return ((nz + 3) & ~3) + kNWIN; }
 
-// row[i] <- sum_k h[k] s[i + 2 kHL - k], i < nz, from the staged row s
-__device__ __forceinline__ void correct_from(const float* s, float* row, int nz, const float* __restrict__ h) {
-    for (int i = 4 * threadIdx.x; i < nz; i += 4 * blockDim.x) {
+// row[i] <- sum_k h[k] s[i + 2 kHL - k], i < nz, from the staged row s; threads tid of nt share it
+__device__ __forceinline__ void correct_from(const float* s, float* row, int nz, const float* __restrict__ h, int tid,
+                                             int nt) {
+    for (int i = 4 * tid; i < nz; i += 4 * nt) {
         float w[kNWIN];
 #pragma unroll
         for (int q = 0; q < kNWIN / 4; ++q) {
@@ -181,6 +182,10 @@ __device__ __forceinline__ void correct_from(const float* s, float* row, int nz,
     }
 }
 
+__device__ __forceinline__ void correct_from(const float* s, float* row, int nz, const float* __restrict__ h) {
+    correct_from(s, row, nz, h, threadIdx.x, blockDim.x);
+}
+
 __device__ __forceinline__ void correct_row(float* row, int nz, const float* __restrict__ h, float* s) {
     for (int k = threadIdx.x; k < corr_floats(nz); k += blockDim.x) {
         const int gz = k - kHL;
@@ -188,6 +193,34 @@ __device__ __forceinline__ void correct_row(float* row, int nz, const float* __r
     }
     __syncthreads();
     correct_from(s, row, nz, h);
+}
+
+// Several rows per CTA: rows_per_cta groups of tpr threads (tpr a multiple of 32, 4 tpr >= nz for
+// one pass); vec4: rows 16-byte aligned (nz % 4 == 0), staged with 16-byte loads.
+__global__ void __launch_bounds__(256) correct_j1_rows_kernel(CorrP p, long long rows, int tpr, int vec4) {
+    extern __shared__ float4 s4[];
+    const int nz = p.g.nz, cf = corr_floats(nz);
+    const int grp = threadIdx.x / tpr, tid = threadIdx.x - grp * tpr;
+    const long long r = (long long)blockIdx.x * (blockDim.x / tpr) + grp;
+    float* s = reinterpret_cast<float*>(s4) + grp * cf;
+    float* row = p.J1 + r * nz;
+    const bool live = r < rows;
+    if (live) {
+        if (vec4) {
+            // s[kHL + 4 q .. +3] = row[4 q .. +3]; the kHL-float margins are zero
+            for (int q = tid; q < (nz >> 2); q += tpr)
+                *reinterpret_cast<float4*>(s + kHL + 4 * q) = *reinterpret_cast<const float4*>(row + 4 * q);
+            for (int k = tid; k < kHL; k += tpr) s[k] = 0.f;
+            for (int k = kHL + nz + tid; k < cf; k += tpr) s[k] = 0.f;
+        } else {
+            for (int k = tid; k < cf; k += tpr) {
+                const int gz = k - kHL;
+                s[k] = (gz >= 0 && gz < nz) ? row[gz] : 0.f;
+            }
+        }
+    }
+    __syncthreads();
+    if (live) correct_from(s, row, nz, p.h, tid, tpr);
 }
 
 // ------------------------------------------------------------------------------ kernels ---
@@ -206,11 +239,6 @@ __global__ void __launch_bounds__(128) filter_z_batch_kernel(const FiltInst* __r
     if ((long long)blockIdx.x >= 3LL * q.g.nx * q.g.ny) return;
     float* row = q.J + (long long)blockIdx.x * q.g.nz;
     filter_row<float, 128>(row, row, q.g.nz, q.vec4 != 0, buf);
-}
-
-__global__ void __launch_bounds__(256) correct_j1_kernel(CorrP p) {
-    extern __shared__ float4 s4[];
-    correct_row(p.J1 + (long long)blockIdx.x * p.g.nz, p.g.nz, p.h, reinterpret_cast<float*>(s4));
 }
 
 // Batched in-place correction: blockIdx.y = instance, blockIdx.x = z row of that instance.
@@ -302,14 +330,21 @@ cudaError_t launch_filter_current_batch(const FiltInst* inst, int ninst, long lo
 
 cudaError_t launch_correct_j1(const GridP& g, const float* taps, int hlen, float* J1, cudaStream_t s) {
     CorrP p = corr_params(g, taps, hlen, J1);
-    const size_t smem = sizeof(float) * corr_floats(g.nz);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(correct_j1_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const long long rows = (long long)g.nx * g.ny;
+    // threads per row: enough for one pass of four outputs each, in whole warps, at most 256
+    int tpr = (((g.nz + 3) / 4) + 31) / 32 * 32;
+    tpr = tpr > 256 ? 256 : tpr;
+    const int rpc = 256 / tpr;
+    const size_t smem = sizeof(float) * corr_floats(g.nz) * rpc;
+    static size_t opted = 48 * 1024;
+    if (smem > opted) {
+        cudaError_t e = cudaFuncSetAttribute(correct_j1_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
+        opted = smem;
     }
-    long long rows = (long long)g.nx * g.ny;
-    correct_j1_kernel<<<(unsigned)rows, 256, smem, s>>>(p);
+    const int vec4 = (g.nz % 4 == 0 && ((uintptr_t)J1 & 15) == 0) ? 1 : 0;
+    correct_j1_rows_kernel<<<(unsigned)((rows + rpc - 1) / rpc), rpc * tpr, smem, s>>>(p, rows, tpr, vec4);
     return cudaGetLastError();
 }
 
