@@ -964,6 +964,9 @@ __device__ __forceinline__ float2 tile_interp3_fixed(const float* __restrict__ F
     return acc;
 }
 
+constexpr int F_CAP3 = 10240;      // general path: field box floats (6 components)
+constexpr int J_CAP3 = 11264;      // general path: current box ints (3 components)
+
 // Global-memory gather and deposition for chunks whose boxes do not fit the shared-memory
 // tiles.  Kept out of line: inlined, their registers would be reserved by the whole kernel.
 template <int SHAPE>
@@ -977,14 +980,15 @@ __device__ __noinline__ void deposit3_global(const GridP g, float qv, const Pos 
     deposit<3, SHAPE>(g, qv, 0.f, p0, p1, acc);
 }
 
-// DEFER: a chunk whose boxes do not fit is appended to defer[2..] (count in defer[0]) and left for
-// push_deposit_3d_deferred_kernel; otherwise it takes the out-of-line global-memory path here.
+// DEFER: a chunk whose boxes do not fit is appended to defer[2..] (count in defer[0]) for the
+// general kernel, or to defer2[2..] for the per-particle kernel when even the general path's boxes
+// would not hold it; without DEFER it takes the out-of-line global-memory path here.
 template <int SHAPE, bool DEFER>
 __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const SpeciesP& sp,
                                                        const float* __restrict__ E, const float* __restrict__ B,
                                                        float* __restrict__ J, int shift, long long chunk0,
                                                        long long stride, float* sF, float* sJ, int* box,
-                                                       int* __restrict__ defer) {
+                                                       int* __restrict__ defer, int* __restrict__ defer2) {
     constexpr int K = Shape<SHAPE>::K;
     constexpr int KW = K + 1;
     const long long n = *sp.count;
@@ -1081,7 +1085,14 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
         const int jzl = bc[1] + 3 - jz0, jxl = bc[3] - bc[2] + 4, jyl = bc[5] - bc[4] + 4;
         const bool jtile = any && jzl <= JZ3 && jxl <= JX3 && jyl <= JY3;
         if (DEFER && any && !(ftile && jtile)) {
-            if (threadIdx.x == 0) defer[2 + atomicAdd(defer, 1)] = (int)(base / FUSED_T);
+            // boxes the general path holds in shared memory (its own rounding of the z extents) go to
+            // the general kernel's list, the rest (the plasma injected since the last sort: one
+            // long row of cells) to the per-particle kernel's list
+            const int gfz = (bc[1] + 1 - fz0 + 3) & ~3, gjz = (bc[1] + 3 - jz0 + 3) & ~3;
+            const bool general = 6 * gfz * fxl * fyl <= F_CAP3 && fxl <= g.nx + 2 * K && fyl <= g.ny + 2 * K &&
+                                 3 * gjz * jxl * jyl <= J_CAP3 && jxl <= g.nx + 2 * KW && jyl <= g.ny + 2 * KW;
+            int* list = general ? defer : defer2;
+            if (threadIdx.x == 0) list[2 + atomicAdd(list, 1)] = (int)(base / FUSED_T);
             __syncthreads();                       // everyone has read this chunk's box words
             continue;
         }
@@ -1313,16 +1324,47 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
 template <int SHAPE>
 __global__ void __launch_bounds__(FUSED_T, 3) push_deposit_3d_kernel(GridP g, SpeciesP sp, const float* __restrict__ E,
                                                                      const float* __restrict__ B, float* __restrict__ J,
-                                                                     int shift, int* __restrict__ defer) {
+                                                                     int shift, int* __restrict__ defer,
+                                                                     int* __restrict__ defer2) {
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     __shared__ int box[14];
     push_deposit_3d_chunks<SHAPE, true>(g, sp, E, B, J, shift, blockIdx.x, gridDim.x, smem, smem + 6 * FV3, box,
-                                        defer);
+                                        defer, defer2);
 }
 
-constexpr int F_CAP3 = 8192;       // general path: field box floats (6 components)
-constexpr int J_CAP3 = 9216;       // general path: current box ints (3 components)
+// The chunks of defer2 (see push_deposit_3d_chunks): per particle, gather from global memory, push,
+// move and deposit with global atomics (contributions that are exactly zero are not added); a
+// light kernel at full occupancy.  The last CTA to finish clears the list (defer2[1] counts CTAs).
+template <int SHAPE>
+__global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_particles_kernel(GridP g, SpeciesP sp,
+                                                                            const float* __restrict__ E,
+                                                                            const float* __restrict__ B,
+                                                                            float* __restrict__ J, int shift,
+                                                                            int* __restrict__ defer2) {
+    const int nd = *(volatile int*)defer2;
+    const long long n = *sp.count;
+    for (int k = blockIdx.x; k < nd; k += gridDim.x) {
+        const long long p = (long long)defer2[2 + k] * FUSED_T + threadIdx.x;
+        if (p >= n) continue;
+        Pos p0, p1;
+        float v3;
+        if (advance_one<3, SHAPE, MODE_FUSED>(g, sp, E, B, shift, p, sp.cap, p0, p1, v3)) {
+            GlobalAcc acc{&g, J};
+            deposit<3, SHAPE>(g, sp.qv, v3, p0, p1, acc);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(defer2 + 1, 1) == (int)gridDim.x - 1) {
+            defer2[0] = 0;
+            defer2[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
 constexpr int SMEM_3D_GEN = F_CAP3 + J_CAP3 + 2 * PF3 * FUSED_T;
 
 // .x = sum Wza Wxa Wya Fa, .y = sum Wzb Wxb Wyb Fb over K^3 nodes of [y][x][z] boxes (row fzl,
@@ -1672,7 +1714,7 @@ __global__ void __launch_bounds__(FUSED_T, 2) push_deposit_3d_batch_kernel(const
     const PartInst& q = inst[blockIdx.y];
     const GridP g = prep_device(q.g);
     push_deposit_3d_chunks<SHAPE, false>(g, q.sp, q.E[parity], q.B[parity], q.J, 0, blockIdx.x, gridDim.x, smem,
-                                         smem + 6 * FV3, box, nullptr);
+                                         smem + 6 * FV3, box, nullptr, nullptr);
 }
 
 template <int SHAPE>
@@ -1751,23 +1793,47 @@ __global__ void __launch_bounds__(256) deposit_kernel(GridP g, SpeciesP sp, floa
         deposit_one<NDIM, SHAPE>(g, sp, J, p);
 }
 
-// Cold plasma for the new front column, slot order (k, j, a, b, c) -> t.
-__global__ void inject_kernel(GridP g, SpeciesP sp, int pz, int px, int py, long long nnew,
-                              long long next_id, int* status) {
-    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nnew) return;
-    long long base = *sp.count;
+// Cold plasma for the new front column.  Particle (k, j, a, b, c) (cell (nz, j, k), sub-cell
+// position (a, b, c)) gets id next_id + canonical index ((k nx + j) P + (a px + b) py + c), P the
+// particles per cell.  Its slot: the block starts at the old count rounded up to `align` (the gap
+// filled with dead slots) and runs through patches of pxc x pyc cells (x-fastest patches, within
+// a patch y, x, then the sub-cell index), clipped at the grid's edges.  In 3D, with align = 256
+// and pxc pyc P <= 256, every 256 consecutive slots of the block then cover one compact patch of
+// the new column, as after a sort, instead of a long row of cells.
+__global__ void inject_kernel(GridP g, SpeciesP sp, int pz, int px, int py, int pxc, int pyc, int align,
+                              long long nnew, long long next_id, int* status) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nnew + align - 1) return;
+    const long long base0 = *sp.count;
+    const long long base = (base0 + align - 1) / align * align;
     if (base + nnew > sp.cap) {
         if (t == 0) atomicOr(status, STATUS_CAPACITY);
         return;
     }
-    long long r = t;
-    int c = (int)(r % py); r /= py;
-    int b = (int)(r % px); r /= px;
-    int a = (int)(r % pz); r /= pz;
-    int j = (int)(r % g.nx); r /= g.nx;
-    int k = (int)r;
-    long long s = base + t;
+    long long s;
+    if (t >= nnew) {                                   // the gap before the aligned block
+        s = base0 + (t - nnew);
+        if (s >= base) return;
+        sp.cell[s] = -1;
+        if (sp.id) sp.id[s] = -1;
+        sp.off[s] = sp.off[sp.cap + s] = 0.f;
+        if (g.ndim == 3) sp.off[2 * sp.cap + s] = 0.f;
+        sp.u[s] = sp.u[sp.cap + s] = sp.u[2 * sp.cap + s] = 0.f;
+        return;
+    }
+    const int P = pz * px * py, ny = g.ndim == 3 ? g.ny : 1;
+    const long long band = (long long)pyc * g.nx * P;  // slots of one row of patches
+    const int pb = (int)(t / band);
+    long long r = t - pb * band;
+    const int hb = min(pyc, ny - pb * pyc);
+    const long long pw = (long long)pxc * hb * P;       // slots of a full-width patch of this row
+    const int pa = (int)(r / pw);
+    r -= pa * pw;
+    const int wa = min(pxc, g.nx - pa * pxc);
+    const int sub = (int)(r % P), cidx = (int)(r / P);
+    const int j = pa * pxc + cidx % wa, k = pb * pyc + cidx / wa;
+    const int c = sub % py, b = (sub / py) % px, a = sub / (py * px);
+    s = base + t;
     sp.cell[s] = encode(g, g.nz, j, k);   // iz = nz: the pending shift brings it to nz - 1
     sp.off[s] = (a + 0.5f) / pz;
     sp.off[sp.cap + s] = (b + 0.5f) / px;
@@ -1775,11 +1841,12 @@ __global__ void inject_kernel(GridP g, SpeciesP sp, int pz, int px, int py, long
     sp.u[s] = 0.f;
     sp.u[sp.cap + s] = 0.f;
     sp.u[2 * sp.cap + s] = 0.f;
-    if (sp.id) sp.id[s] = (int32_t)(next_id + t);
+    if (sp.id) sp.id[s] = (int32_t)(next_id + ((long long)k * g.nx + j) * P + sub);
 }
 
-__global__ void add_count_kernel(int32_t* count, long long nnew, long long cap) {
-    if (*count + nnew <= cap) *count += (int32_t)nnew;
+__global__ void add_count_kernel(int32_t* count, long long nnew, int align, long long cap) {
+    const long long base = ((long long)*count + align - 1) / align * align;
+    if (base + nnew <= cap) *count = (int32_t)(base + nnew);
 }
 
 // ---- counting sort by tiles of cells: 8 x 8 (z, x) in 2D, 4 x 4 x 4 in 3D, z-fastest ----
@@ -2017,7 +2084,9 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
                 if (e != cudaSuccess) return e;
                 configured = true;
             }
-            k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift, defer);
+            // two lists of deferred chunks, each 2 + ceil(cap / FUSED_T) ints
+            int* defer2 = defer + 2 + (sp.cap + FUSED_T - 1) / FUSED_T;
+            k<<<pblocks(extent), FUSED_T, smem, s>>>(g, sp, E, B, J, shift, defer, defer2);
             // the deferred chunks: a fixed grid (their count is on the device)
             auto kd = push_deposit_3d_deferred_kernel<SH>;
             const size_t smem_d = SMEM_3D_GEN * sizeof(float);
@@ -2030,6 +2099,8 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
             const long long nchunk = (extent + FUSED_T - 1) / FUSED_T;
             const unsigned nb = (unsigned)(nchunk < 152 * 2 ? (nchunk < 1 ? 1 : nchunk) : 152 * 2);
             kd<<<nb, FUSED_T, smem_d, s>>>(g, sp, E, B, J, shift, defer);
+            const unsigned nb2 = (unsigned)(nchunk < 152 * 8 ? (nchunk < 1 ? 1 : nchunk) : 152 * 8);
+            push_deposit_3d_particles_kernel<SH><<<nb2, FUSED_T, 0, s>>>(g, sp, E, B, J, shift, defer2);
         } else {
             push_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, shift);
         }
@@ -2089,12 +2160,29 @@ cudaError_t launch_deposit_unfused(const GridP& g0, const SpeciesP& sp, float* J
 }
 
 cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], long long next_id,
-                          int* status, cudaStream_t s) {
+                          int* status, long long* extent, cudaStream_t s) {
     int pz = ppc[0], px = ppc[1], py = g.ndim == 3 ? ppc[2] : 1;
-    long long nnew = (long long)g.nx * (g.ndim == 3 ? g.ny : 1) * pz * px * py;
+    const long long P = (long long)pz * px * py;
+    long long nnew = (long long)g.nx * (g.ndim == 3 ? g.ny : 1) * P;
     if (nnew <= 0) return cudaSuccess;
-    inject_kernel<<<nblocks(nnew, 256), 256, 0, s>>>(g, sp, pz, px, py, nnew, next_id, status);
-    add_count_kernel<<<1, 1, 0, s>>>(sp.count, nnew, sp.cap);
+    // 2D: one patch per row, no alignment (the canonical order); 3D: the largest power-of-two
+    // patch, x side >= y side, whose particles fill at most one 256-particle chunk
+    int pxc = g.nx, pyc = 1, align = 1;
+    if (g.ndim == 3) {
+        pxc = 1;
+        align = FUSED_T;
+        for (;;) {
+            const bool gx = 2 * pxc <= g.nx, gy = 2 * pyc <= g.ny;
+            if (2 * pxc * pyc * P > FUSED_T || (!gx && !gy)) break;
+            if (gx && (pxc <= pyc || !gy)) pxc *= 2;
+            else pyc *= 2;
+        }
+    }
+    inject_kernel<<<nblocks(nnew + align - 1, 256), 256, 0, s>>>(g, sp, pz, px, py, pxc, pyc, align, nnew, next_id,
+                                                                 status);
+    add_count_kernel<<<1, 1, 0, s>>>(sp.count, nnew, align, sp.cap);
+    const long long ext = (*extent + align - 1) / align * align + nnew;
+    *extent = ext < sp.cap ? ext : sp.cap;
     return cudaGetLastError();
 }
 

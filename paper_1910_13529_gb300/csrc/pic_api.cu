@@ -213,13 +213,12 @@ pic_status advance_fields(pic_t* h, const float* Ein, const float* Bin, float* E
             SpeciesP sp = species_params(h, is);
             {
                 Scope sc(h, PIC_T_WINDOW, 2, s);
-                CK(h, launch_inject(h->g, sp, h->cfg.inject_ppc, h->next_id, h->status, s), "inject kernel");
+                CK(h, launch_inject(h->g, sp, h->cfg.inject_ppc, h->next_id, h->status, &h->sp[is].extent, s),
+                   "inject kernel");
             }
             long long nnew = (long long)h->cfg.nx * (h->cfg.ndim == 3 ? h->cfg.ny : 1) * h->cfg.inject_ppc[0] *
                              h->cfg.inject_ppc[1] * (h->cfg.ndim == 3 ? h->cfg.inject_ppc[2] : 1);
             h->next_id += nnew;
-            long long ext = h->sp[is].extent + nnew;
-            h->sp[is].extent = ext < h->sp[is].cap ? ext : h->sp[is].cap;
         }
     }
     return PIC_OK;
@@ -591,11 +590,13 @@ pic_status pic_step(pic_t* h, int nsteps, void* stream) {
             if (!h->sp[i].bound) continue;
             SpeciesSlot& q = h->sp[i];
             if (h->cfg.ndim == 3 && !q.defer) {
-                if ((st = dalloc(h, &q.defer, 2 + (q.cap + 255) / 256, "deferred chunk list"))) return st;
+                const long long len = 2 + (q.cap + 255) / 256;       // two lists of this length
+                if ((st = dalloc(h, &q.defer, 2 * len, "deferred chunk lists"))) return st;
                 CK(h, cudaMemsetAsync(q.defer, 0, sizeof(int32_t) * 2, s), "clear deferred chunk list");
+                CK(h, cudaMemsetAsync(q.defer + len, 0, sizeof(int32_t) * 2, s), "clear deferred chunk list");
             }
             SpeciesP sp = species_params(h, i);
-            Scope sc(h, PIC_T_PARTICLES, h->cfg.ndim == 3 ? 2 : 1, s);
+            Scope sc(h, PIC_T_PARTICLES, h->cfg.ndim == 3 ? 3 : 1, s);
             CK(h, launch_push(h->g, sp, Ec, Bc, h->J, h->pending_shift, 0, q.extent, q.defer, s),
                "fused push/deposit kernel");
         }

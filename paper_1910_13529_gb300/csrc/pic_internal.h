@@ -126,14 +126,17 @@ cudaError_t launch_correct_j1_batch(const CorrInst* inst, int ninst, int max_row
 cudaError_t launch_push_batch(const PartInst* inst, int ninst, int ndim, int shape, long long max_extent, int parity,
                               cudaStream_t s);
 cudaError_t launch_zero_j_batch(const PartInst* inst, int ninst, long long max_ncell, cudaStream_t s);
-// defer (3D fused mode): library scratch of 2 + ceil(cap / 256) ints, zero on first use: the
-// chunks whose shared-memory boxes do not fit, processed by a second kernel that clears the list.
+// defer (3D fused mode): library scratch of two lists of 2 + ceil(cap / 256) ints each, their
+// first two ints zero on first use: the chunks whose shared-memory boxes do not fit, processed by
+// the general and the per-particle kernels, which clear the lists.
 cudaError_t launch_push(const GridP& g, const SpeciesP& sp, const float* E, const float* B,
                         float* J, int shift, int mode, long long extent, int* defer, cudaStream_t s);
 cudaError_t launch_deposit_unfused(const GridP& g, const SpeciesP& sp, float* J, long long extent,
                                    cudaStream_t s);
+// Appends the new column's cold plasma (3D: at the count rounded up to 256, patch-ordered);
+// *extent, the host's upper bound of the count, is advanced accordingly.
 cudaError_t launch_inject(const GridP& g, const SpeciesP& sp, const int ppc[3], long long next_id,
-                          int* status, cudaStream_t s);
+                          int* status, long long* extent, cudaStream_t s);
 long long sort_bins(const GridP& g);
 cudaError_t launch_sort(const GridP& g, const SpeciesP& sp, long long extent, int32_t* hist,
                         int32_t* blocksums, int32_t* cell_alt, float* off_alt, float* u_alt,
