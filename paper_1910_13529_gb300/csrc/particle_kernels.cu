@@ -507,6 +507,16 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+// 16- and 4-byte copies with zero fill (valid = false reads nothing and writes zeros): field
+// groups of a staged box, cells outside 0 <= z < nz read as zero
+__device__ __forceinline__ void cp_async16z(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async4z(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all_p() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -1096,25 +1106,52 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
             __syncthreads();                       // everyone has read this chunk's box words
             continue;
         }
-        unsigned fbits = 0u;                       // any nonzero bit among the staged field values
-        if (ftile) {
-            // groups (c, y, x, z4) of the [c][y][x][z] box, only those inside the used extents
+        // groups (c, y, x, z4) of the [c][y][x][z] box, only those inside the used extents, copied
+        // asynchronously (all of a thread's groups in flight at once); z groups start at multiples of
+        // 4, so with nz % 4 == 0 a group lies wholly inside or wholly outside 0 <= z < nz
+        auto staged = [&](auto&& f) {
 #pragma unroll 2
             for (int i = threadIdx.x; i < 6 * FY3 * FX3 * (FZ3 / 4); i += FUSED_T) {
                 const int zg = i % (FZ3 / 4), r = i / (FZ3 / 4);
                 const int x = r & (FX3 - 1), y = (r >> 3) & (FY3 - 1), c = r >> 6;
                 if (4 * zg >= fzl || x >= fxl || y >= fyl) continue;
+                f(c, x, y, zg);
+            }
+        };
+        static_assert(FX3 == 8 && FY3 == 8, "staging index decomposition");
+        if (ftile) {
+            staged([&](int c, int x, int y, int zg) {
                 const long long row = ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
                 const float* f = (c < 3 ? E + c * N : B + (c - 3) * N) + row;
-                const float4 v = load_group(f, fz0 + 4 * zg, g.nz, fvec);
-                fbits |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
-                *reinterpret_cast<float4*>(sF + c * FV3 + (y * FX3 + x) * FZP3 + 4 * zg) = v;
-            }
+                float* d = sF + c * FV3 + (y * FX3 + x) * FZP3 + 4 * zg;
+                const int gz = fz0 + 4 * zg;
+                if (fvec) {
+                    const bool in = gz >= 0 && gz < g.nz;
+                    cp_async16z(d, f + (in ? gz : 0), in);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool in = (unsigned)(gz + j) < (unsigned)g.nz;
+                        cp_async4z(d + j, f + (in ? gz + j : 0), in);
+                    }
+                }
+            });
         }
-        static_assert(FX3 == 8 && FY3 == 8, "staging index decomposition");
-        // a particle at rest in zero fields stays at rest and carries no current
+        cp_async_commit();
+        cp_async_wait_all_p();                     // the box (and the next chunk's particle words)
+        // a particle at rest in zero fields stays at rest and carries no current: a chunk with no
+        // moving particle reads its staged groups back to see whether they are all zero
         const bool moving = ok && (u[0] != 0.f || u[1] != 0.f || u[2] != 0.f);
-        if (!__syncthreads_or(fbits != 0u || moving) && ftile) {
+        bool live = __syncthreads_or(moving);
+        if (!live && ftile) {
+            unsigned fbits = 0u;
+            staged([&](int c, int x, int y, int zg) {
+                const float4 v = *reinterpret_cast<const float4*>(sF + c * FV3 + (y * FX3 + x) * FZP3 + 4 * zg);
+                fbits |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+            });
+            live = __syncthreads_or(fbits != 0u);
+        }
+        if (!live && ftile) {
             // a quiet chunk (every particle at rest, every field of its footprint zero): nothing
             // moves and no current flows; only a pending window shift is applied to the cells,
             // and the rest of the chunk runs with every particle switched off
