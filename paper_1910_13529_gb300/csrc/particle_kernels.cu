@@ -949,6 +949,28 @@ constexpr int PF3 = 7;                           // prefetched words per particl
 constexpr int SMEM_3D = 6 * FV3 + 3 * JV3 + 2 * PF3 * FUSED_T;
 static_assert((3 * JV3) % 4 == 0 && FZP3 % 4 == 0 && JZP3 % 4 == 0, "16-byte groups");
 
+// i / d for the box extents d = 1..32 as (i m_d) >> 16 with m_d = ceil(2^16 / d): the product
+// exceeds i / d by i e / (2^16 d), e = d m_d - 2^16 < d, which keeps it below the next integer
+// (at least 1/d above i / d) while i e < 2^16, i.e. for every i < 2048 (checked below).
+struct Inv16 {
+    unsigned m[33];
+};
+constexpr Inv16 make_inv16() {
+    Inv16 t{};
+    for (int d = 1; d <= 32; ++d) t.m[d] = 65535u / (unsigned)d + 1u;
+    return t;
+}
+constexpr bool inv16_exact() {
+    const Inv16 t = make_inv16();
+    for (unsigned d = 1; d <= 32; ++d)
+        for (unsigned i = 0; i < 2048; ++i)
+            if (((i * t.m[d]) >> 16) != i / d) return false;
+    return true;
+}
+static_assert(inv16_exact(), "reciprocal division table");
+__constant__ Inv16 kInv16 = make_inv16();
+__device__ __forceinline__ int qdiv(int i, unsigned m) { return (int)(((unsigned)i * m) >> 16); }
+
 // .x = sum Wza Wxa Wya Fa, .y = sum Wzb Wxb Wyb Fb over K^3 nodes of the fixed-stride field box;
 // oa, ob: offsets of the two stencil origins.
 template <int K>
@@ -1109,16 +1131,20 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
         // groups (c, y, x, z4) of the [c][y][x][z] box, only those inside the used extents, copied
         // asynchronously (all of a thread's groups in flight at once); z groups start at multiples of
         // 4, so with nz % 4 == 0 a group lies wholly inside or wholly outside 0 <= z < nz
+        const int ngz = ftile ? (fzl + 3) >> 2 : 0;
+        const unsigned mgz = ftile ? kInv16.m[ngz] : 0u, mfx = ftile ? kInv16.m[fxl] : 0u,
+                       mfy = ftile ? kInv16.m[fyl] : 0u;
+        const int nstage = 6 * fyl * fxl * ngz;
         auto staged = [&](auto&& f) {
 #pragma unroll 2
-            for (int i = threadIdx.x; i < 6 * FY3 * FX3 * (FZ3 / 4); i += FUSED_T) {
-                const int zg = i % (FZ3 / 4), r = i / (FZ3 / 4);
-                const int x = r & (FX3 - 1), y = (r >> 3) & (FY3 - 1), c = r >> 6;
-                if (4 * zg >= fzl || x >= fxl || y >= fyl) continue;
+            for (int i = threadIdx.x; i < nstage; i += FUSED_T) {
+                const int r = qdiv(i, mgz), zg = i - r * ngz;
+                const int r2 = qdiv(r, mfx), x = r - r2 * fxl;
+                const int c = qdiv(r2, mfy), y = r2 - c * fyl;
                 f(c, x, y, zg);
             }
         };
-        static_assert(FX3 == 8 && FY3 == 8, "staging index decomposition");
+        static_assert(6 * FY3 * FX3 * (FZ3 / 4) < 2048 && FX3 <= 32 && FY3 <= 32 && FZ3 / 4 <= 32, "qdiv range");
         if (ftile) {
             staged([&](int c, int x, int y, int zg) {
                 const long long row = ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
@@ -1331,11 +1357,12 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
             // box -> J in 16-byte groups (one vector atomic per group inside the grid); the groups
             // are cleared as they are read, for the next chunk
             const int ng = (jzl + 3) >> 2;
-            for (int i = threadIdx.x; i < 3 * JY3 * JX3 * (JZ3 / 4); i += FUSED_T) {
-                const int zg = i % (JZ3 / 4), r = i / (JZ3 / 4);
-                const int x = r % JX3, rr = r / JX3;
-                const int y = rr % JY3, c = rr / JY3;
-                if (zg >= ng || x >= jxl || y >= jyl) continue;
+            const unsigned mg = kInv16.m[ng], mjx = kInv16.m[jxl], mjy = kInv16.m[jyl];
+            static_assert(3 * JY3 * JX3 * (JZ3 / 4) < 2048 && JX3 <= 32 && JY3 <= 32 && JZ3 / 4 <= 32, "qdiv range");
+            for (int i = threadIdx.x; i < 3 * jyl * jxl * ng; i += FUSED_T) {
+                const int r = qdiv(i, mg), zg = i - r * ng;
+                const int r2 = qdiv(r, mjx), x = r - r2 * jxl;
+                const int c = qdiv(r2, mjy), y = r2 - c * jyl;
                 int4* grp = reinterpret_cast<int4*>(iJ + c * JV3 + (y * JX3 + x) * JZP3) + zg;
                 const int4 q = *grp;
                 if ((q.x | q.y | q.z | q.w) == 0) continue;
