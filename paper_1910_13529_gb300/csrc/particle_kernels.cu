@@ -1562,23 +1562,60 @@ __device__ __forceinline__ void push_deposit_3d_general(const GridP& g, const Sp
         const int jxl = any ? bc[3] - bc[2] + 4 : 0, jyl = any ? bc[5] - bc[4] + 4 : 0;
         const int jvol = jzl * jxl * jyl;
         const bool jtile = any && 3 * jvol <= J_CAP3 && jxl <= g.nx + 2 * KW && jyl <= g.ny + 2 * KW;
-        if (ftile) {
-            const int ng = fzl >> 2, rows = fyl * fxl;
-            const float rg = 1.f / (float)ng, rr = 1.f / (float)rows, rx = 1.f / (float)fxl;
+        // groups (c, y, x, z4) of the [c][y][x][z] box, copied asynchronously (all of a thread's
+        // groups in flight at once); z groups start at multiples of 4, so with nz % 4 == 0 a group
+        // lies wholly inside or wholly outside 0 <= z < nz
+        const int ng = fzl >> 2, rows = fyl * fxl;
+        const float rg = 1.f / (float)max(ng, 1), rr = 1.f / (float)max(rows, 1), rx = 1.f / (float)max(fxl, 1);
+        auto staged = [&](auto&& f) {
             for (int i = threadIdx.x; i < 6 * rows * ng; i += FUSED_T) {
                 const int r = box_div(i, rg), zg = i - r * ng;
                 const int c = box_div(r, rr), q = r - c * rows;
-                const int y = box_div(q, rx), x = q - y * fxl;
-                const long long row =
-                    ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
-                const float* f = (c < 3 ? E + c * N : B + (c - 3) * N) + row;
-                *reinterpret_cast<float4*>(sF + c * fvol + q * fzl + 4 * zg) = load_group(f, fz0 + 4 * zg, g.nz, fvec);
+                f(c, q, zg);
             }
+        };
+        if (ftile) {
+            staged([&](int c, int q, int zg) {
+                const int y = box_div(q, rx), x = q - y * fxl;
+                const long long row = ((long long)wrapi(fy0 + y, g.ny) * g.nx + wrapi(fx0 + x, g.nx)) * g.nz;
+                const float* f = (c < 3 ? E + c * N : B + (c - 3) * N) + row;
+                float* d = sF + c * fvol + q * fzl + 4 * zg;
+                const int gz = fz0 + 4 * zg;
+                if (fvec) {
+                    const bool in = gz >= 0 && gz < g.nz;
+                    cp_async16z(d, f + (in ? gz : 0), in);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool in = (unsigned)(gz + j) < (unsigned)g.nz;
+                        cp_async4z(d + j, f + (in ? gz + j : 0), in);
+                    }
+                }
+            });
         }
+        cp_async_commit();
         if (jtile)
             for (int i = threadIdx.x; i < (3 * jvol) >> 2; i += FUSED_T)
                 reinterpret_cast<float4*>(sJ)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncthreads();
+        cp_async_wait_all_p();                     // the box (and the next chunk's particle words)
+        // a quiet chunk (every particle at rest, every field of its footprint zero; the plasma
+        // injected at the front since the last sort): only a pending window shift is applied to
+        // the cells, and the rest of the chunk runs with every particle switched off.  The staged
+        // groups are read back only when no particle of the chunk moves.
+        const bool moving = ok && (u[0] != 0.f || u[1] != 0.f || u[2] != 0.f);
+        bool live = __syncthreads_or(moving);
+        if (!live && ftile) {
+            unsigned fbits = 0u;
+            staged([&](int c, int q, int zg) {
+                const float4 v = *reinterpret_cast<const float4*>(sF + c * fvol + q * fzl + 4 * zg);
+                fbits |= __float_as_uint(v.x) | __float_as_uint(v.y) | __float_as_uint(v.z) | __float_as_uint(v.w);
+            });
+            live = __syncthreads_or(fbits != 0u);
+        }
+        if (!live && ftile) {
+            if (shift && ok) sp.cell[p] = encode(g, p0.iz, p0.ix, p0.iy);
+            ok = false;
+        }
         // ---- gather (E1 z+, E2 x+, E3 y+, B1 x+ y+, B2 z+ y+, B3 z+ x+) ----
         float eb[6];
         if (ok) {
