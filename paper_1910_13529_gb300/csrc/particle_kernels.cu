@@ -2072,29 +2072,46 @@ __global__ void scatter_kernel(GridP g, SpeciesP sp, int32_t* cursor, int32_t* c
         first = __shfl_sync(0xffffffffu, first, leader);
         if (key < 0) continue;
         const long long d = (long long)first + __popc(grp & ((1u << lane) - 1u));
+        // every load before the first store: the source and destination arrays are distinct, and
+        // the loads then overlap instead of waiting on one another's stores
+        float o[NDIM], w[3];
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) o[k] = __ldg(sp.off + k * cap + p);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) w[k] = __ldg(sp.u + k * cap + p);
+        const int32_t idv = id2 ? __ldg(sp.id + p) : 0;
         cell2[d] = c;
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) off2[k * cap + d] = sp.off[k * cap + p];
+        for (int k = 0; k < NDIM; ++k) off2[k * cap + d] = o[k];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) u2[k * cap + d] = sp.u[k * cap + p];
-        if (id2) id2[d] = sp.id[p];
+        for (int k = 0; k < 3; ++k) u2[k * cap + d] = w[k];
+        if (id2) id2[d] = idv;
     }
 }
 
 // copy the sorted slots [0, total) back into the caller's arrays and set the count
+// (every load before the first store, as in scatter_kernel)
 template <int NDIM>
-__global__ void copy_back_kernel(SpeciesP sp, const int32_t* total, const int32_t* cell2, const float* off2,
-                                 const float* u2, const int32_t* id2) {
+__global__ void copy_back_kernel(SpeciesP sp, const int32_t* total, const int32_t* __restrict__ cell2,
+                                 const float* __restrict__ off2, const float* __restrict__ u2,
+                                 const int32_t* __restrict__ id2) {
     const long long n = *total;
     const long long cap = sp.cap;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
-        sp.cell[p] = cell2[p];
+        const int32_t c = __ldg(cell2 + p);
+        float o[NDIM], w[3];
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) sp.off[k * cap + p] = off2[k * cap + p];
+        for (int k = 0; k < NDIM; ++k) o[k] = __ldg(off2 + k * cap + p);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) sp.u[k * cap + p] = u2[k * cap + p];
-        if (id2) sp.id[p] = id2[p];
+        for (int k = 0; k < 3; ++k) w[k] = __ldg(u2 + k * cap + p);
+        const int32_t idv = id2 ? __ldg(id2 + p) : 0;
+        sp.cell[p] = c;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) sp.off[k * cap + p] = o[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sp.u[k * cap + p] = w[k];
+        if (id2) sp.id[p] = idv;
     }
 }
 

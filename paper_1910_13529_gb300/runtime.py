@@ -280,11 +280,11 @@ class StencilLoss:
         from . import pic_adjoint_step
         sim = self._sim(C)
         ckpt = []
-        for n in range(self.nsteps):
-            if n % self.every == 0:
-                ckpt.append((n, sim.E.clone(), sim.B.clone(),
-                             {s: {k: sim.species[s][k].clone() for k in ("cell", "off", "u")} for s in sim.species}))
-            sim.step(1)
+        # forward in runs of `every` steps (an even run ends in the bound field arrays: no copy back)
+        for n0 in range(0, self.nsteps, self.every):
+            ckpt.append((n0, sim.E.clone(), sim.B.clone(),
+                         {s: {k: sim.species[s][k].clone() for k in ("cell", "off", "u")} for s in sim.species}))
+            sim.step(min(self.every, self.nsteps - n0))
         zc = self._mask_z(sim)
         L, dV = self._loss(sim, zc)
         aE = torch.zeros_like(sim.E)
