@@ -644,6 +644,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.current_stream(dev).synchronize()
         pic_bind_species(sim.h, s, d["cell"].data_ptr(), d["off"].data_ptr(), d["u"].data_ptr(), None, n0[s],
                          d["cap"], sps[s]["q"], sps[s]["m"], sps[s]["w"])
+    sim.sort()                      # the uploaded particles come in generation order: sort them first
     sim.step(args.steps)
     oE.copy_(sim.E, non_blocking=True)
     oB.copy_(sim.B, non_blocking=True)

@@ -197,8 +197,9 @@ pic_status pic_step(pic_t* h, int nsteps, void* stream);
  * deposit when the handle is configured with the filter.  Zero current outside 0 <= i < nz. */
 pic_status pic_filter_current(pic_t* h, void* stream);
 /* Counting sort of every species (dead slots removed; ids follow their particles).  Order: tiles
- * of 8 x 8 (z, x) cells in 2D and 4 x 4 x 4 (z, x, y) cells in 3D, tiles z-fastest then x then
- * y, cells z-fastest then x then y inside a tile. */
+ * of 8 x 8 (z, x) cells in 2D and 4 x 4 x 4 (z, x, y) cells in 3D in columns along z, columns
+ * along x then y; the tile order snakes (z reversed in odd columns, x reversed in odd rows of
+ * columns: consecutive tiles are neighbours); cells z-fastest then x then y inside a tile. */
 pic_status pic_sort(pic_t* h, void* stream);
 
 /* ---- diagnostics (FP64 on the GPU) ----------------------------------------------------

@@ -1280,14 +1280,9 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
             // P = S0 + dS/2 and Q = S0/2 + dS/3 of an axis, formed where they are used
             auto P_ = [](float s0, float ds) { return fmaf(0.5f, ds, s0); };
             auto Q_ = [](float s0, float ds) { return fmaf(1.f / 3.f, ds, 0.5f * s0); };
-            // window origins are >= -2 and below 2^20 - 4 on every axis: an exact 64-bit key
-            const unsigned long long key =
-                ok ? (((unsigned long long)(bz + 4) << 40) | ((unsigned long long)(bx + 4) << 20) |
-                      (unsigned long long)(by + 4))
-                   : (0xFFFFF00000000000ull | (unsigned)threadIdx.x);
-            // direct atomics when at most 4 lanes share a window (144 deposits per particle make
-            // conflicts costlier than in 2D), else sums over runs of lanes first
-            const int gmax = __reduce_max_sync(0xffffffffu, __popc(__match_any_sync(0xffffffffu, key)));
+            // Every lane adds its own deposits, also where many lanes of a warp share a window (the
+            // dense beam): the shared-memory atomic unit serialises equal addresses, which costs less
+            // than summing over the lanes of a window first (measured on the beam in plasma).
             int* s0 = iJ + ((by - jy0) * JX3 + (bx - jx0)) * JZP3 + (bz - jz0);
             const float MAGIC = 12582912.f;           // 1.5 2^23
             // When no lane of the warp changes its support node along an axis, the last node of the
@@ -1340,15 +1335,7 @@ __device__ __forceinline__ void push_deposit_3d_chunks(const GridP& g, const Spe
                     }
                 }
             };
-            if (gmax <= 4) {
-                if (ok) terms([&](int o, float biased) { atomicAdd(s0 + o, __float_as_int(biased) - 0x4B400000); });
-            } else {
-                const SegReduce seg = make_segments(key);
-                terms([&](int o, float biased) {
-                    const int v = seg.sum(__float_as_int(biased) - 0x4B400000);
-                    if (seg.head && ok && v != 0) atomicAdd(s0 + o, v);
-                });
-            }
+            if (ok) terms([&](int o, float biased) { atomicAdd(s0 + o, __float_as_int(biased) - 0x4B400000); });
         } else if (!DEFER && any && !jtile && ok) {
             deposit3_global<SHAPE>(g, sp.qv, p0, p1, J);
         }
@@ -1950,20 +1937,26 @@ __global__ void add_count_kernel(int32_t* count, long long nnew, int align, long
     if (base + nnew <= cap) *count = (int32_t)(base + nnew);
 }
 
-// ---- counting sort by tiles of cells: 8 x 8 (z, x) in 2D, 4 x 4 x 4 in 3D, z-fastest ----
+// ---- counting sort by tiles of cells: 8 x 8 (z, x) in 2D, 4 x 4 x 4 in 3D ----
 // (a chunk of consecutive particles then covers a compact patch, which keeps the shared-memory
 // boxes of the fused kernels small; in 3D a cubic tile shrinks the chunk's field and current
-// boxes by about a third against 8 x 8 x 1)
+// boxes by about a third against 8 x 8 x 1).  Tiles run in columns along z; the columns follow x
+// then y, and the order snakes (z reversed in every other column, x in every other row of
+// columns), so consecutive tiles are always neighbours: a chunk that straddles two columns stays
+// compact instead of spanning the front and the back of the window.
 __device__ __forceinline__ int sort_key(const GridP& g, int cell) {
     int izg, ix, iy;
     decode(g, cell, izg, ix, iy);
     if (g.ndim == 3) {          // 4 x 4 x 4-cell tiles: compact 3D chunks
         const int ntz = (g.nzg + 3) >> 2, ntx = (g.nx + 3) >> 2;
-        return (((iy >> 2) * ntx + (ix >> 2)) * ntz + (izg >> 2)) * 64 + ((((iy & 3) << 2) + (ix & 3)) << 2) +
-               (izg & 3);
+        const int ty = iy >> 2, tx = (ty & 1) ? ntx - 1 - (ix >> 2) : ix >> 2;
+        const int col = ty * ntx + tx;
+        const int tz = (col & 1) ? ntz - 1 - (izg >> 2) : izg >> 2;
+        return (col * ntz + tz) * 64 + ((((iy & 3) << 2) + (ix & 3)) << 2) + (izg & 3);
     }
-    const int ntz = (g.nzg + 7) >> 3, ntx = (g.nx + 7) >> 3;
-    return ((iy * ntx + (ix >> 3)) * ntz + (izg >> 3)) * 64 + ((ix & 7) << 3) + (izg & 7);
+    const int ntz = (g.nzg + 7) >> 3, col = ix >> 3;
+    const int tz = (col & 1) ? ntz - 1 - (izg >> 3) : izg >> 3;
+    return (col * ntz + tz) * 64 + ((ix & 7) << 3) + (izg & 7);
 }
 
 // Cell-sorted particles come in runs of equal keys: the lanes of a warp with one key add their
@@ -2217,7 +2210,7 @@ cudaError_t launch_push(const GridP& g0, const SpeciesP& sp, const float* E, con
             const long long nchunk = (extent + FUSED_T - 1) / FUSED_T;
             const unsigned nb = (unsigned)(nchunk < 152 * 2 ? (nchunk < 1 ? 1 : nchunk) : 152 * 2);
             kd<<<nb, FUSED_T, smem_d, s>>>(g, sp, E, B, J, shift, defer);
-            const unsigned nb2 = (unsigned)(nchunk < 152 * 8 ? (nchunk < 1 ? 1 : nchunk) : 152 * 8);
+            const unsigned nb2 = (unsigned)(nchunk < 152 * 4 ? (nchunk < 1 ? 1 : nchunk) : 152 * 4);
             push_deposit_3d_particles_kernel<SH><<<nb2, FUSED_T, 0, s>>>(g, sp, E, B, J, shift, defer2);
         } else {
             push_kernel<ND, SH><<<pblocks(extent), 256, 0, s>>>(g, sp, E, B, shift);

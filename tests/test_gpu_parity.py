@@ -246,7 +246,10 @@ def test_sort_keeps_particles_and_orders_cells():
     p = sim.particles(0)
     assert len(p["cell"]) == n_live and np.all(p["cell"] >= 0)
     iz, ix, _ = decode_cells(p["cell"], sim.nz, sim.nx)
-    tile = (ix // 8) * ((sim.nz + 2 + 7) // 8) + (iz + 1) // 8        # 8 x 8 tiles, z-fastest
+    ntz = (sim.nz + 2 + 7) // 8
+    col = ix // 8
+    tz = np.where(col % 2 == 1, ntz - 1 - (iz + 1) // 8, (iz + 1) // 8)  # 8 x 8 tiles, snaking along z
+    tile = col * ntz + tz
     assert np.all(np.diff(tile) >= 0)
     inner = ((ix % 8) * 8 + (iz + 1) % 8)
     same = np.diff(tile) == 0
@@ -269,7 +272,9 @@ def test_sort_orders_3d_cells_in_cubic_tiles():
     iz, ix, iy = decode_cells(p["cell"], sim.nz, sim.nx)
     izg = iz + 1
     ntz, ntx = (sim.nz + 2 + 3) // 4, (sim.nx + 3) // 4
-    tile = ((iy // 4) * ntx + ix // 4) * ntz + izg // 4             # 4 x 4 x 4 tiles, z-fastest
+    ty = iy // 4
+    col = ty * ntx + np.where(ty % 2 == 1, ntx - 1 - ix // 4, ix // 4)   # 4 x 4 x 4 tiles, snaking
+    tile = col * ntz + np.where(col % 2 == 1, ntz - 1 - izg // 4, izg // 4)
     assert np.all(np.diff(tile) >= 0)
     inner = ((iy % 4) * 4 + ix % 4) * 4 + izg % 4
     same = np.diff(tile) == 0
