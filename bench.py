@@ -278,10 +278,11 @@ TRAFFIC_SOURCES = {
 
 
 def captured_traffic(kind, ndim, units=None):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu summary, or
-    None when there is none or the kernel source has changed since the capture.  A summary taken
-    on a reduced case states the particles of its captured step (units_per_step); the traffic is
-    then scaled to `units` (particles per step of the timed run) in proportion."""
+    """dram__bytes_read.sum + dram__bytes_write.sum of one step of the kernel class (all its
+    launches in that step, the scope of roofline.achieved) from the committed ncu summary, or None
+    when there is none or the kernel source has changed since the capture.  A summary taken on a
+    reduced case states the particles of its captured step (units_per_step); the traffic is then
+    scaled to `units` (particles per step of the timed run) in proportion."""
     import re
     entry = TRAFFIC_SOURCES.get((kind, ndim))
     if entry is None:
@@ -292,7 +293,7 @@ def captured_traffic(kind, ndim, units=None):
         digest = code_sha1(open(src).read())
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(r"traffic_bytes_per_step:\s*([0-9.eE+]+)", text)
     h = re.search(r"code_sha1:\s*([0-9a-f]{40})", text)
     if not m or not h or h.group(1) != digest:
         return None
@@ -412,7 +413,7 @@ def run_beam_secondary(args, dev, wname_sel):
            "ms_per_step": med / args.steps, "cell_updates_per_s": cells * args.steps / (med / 1e3),
            "particle_kernel": {"achieved_GBps": achieved, "frac": achieved / peak, "peak_kind": kind,
                                "ms_per_step": kms["particles"] / args.steps,
-                               "traffic": captured_traffic("particles", grid["ndim"])},
+                               "traffic": captured_traffic("particles", grid["ndim"], units=kcount)},
            "field_advance_GBps": BYTES_PER_CELL_UPDATE * cells * args.steps / (kms["fields"] / 1e3) / 1e9,
            "kernel_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "field_tile_variant": int(tuned[0]), "l2": "working set ~197 MB > 129 MB L2 (partly L2-resident)"}
@@ -703,7 +704,8 @@ def run_ours(args, rank, world, local_rank):
                            "algorithmic_bytes_per_unit": bpp if dom == "particles" else BYTES_PER_CELL_UPDATE,
                            "units_per_step": units_per_step,
                            "launches_per_step": klaunch[dom] / args.steps,
-                           "kernel_ms_per_step": kms[dom] / args.steps},
+                           "kernel_ms_per_step": kms[dom] / args.steps,
+                           "scope": "achieved and traffic: one step of the kernel class (all its launches)"},
               "cpu_baseline": cpu,
               "e2e": {"value": e2e_value, "unit": "particle-pushes/s", "h2d_bytes_per_step": h2d / args.steps,
                       "d2h_bytes_per_step": d2h / args.steps},
