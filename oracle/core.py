@@ -183,8 +183,11 @@ class Species:
 class Sim:
     """Plain FP64 PIC loop over the C oracle routines (one grid, several species)."""
 
-    def __init__(self, g: Grid, species, h=None, moving_window=False, inject=None, filt=False):
+    def __init__(self, g: Grid, species, h=None, moving_window=False, inject=None, filt=False, kspace=None):
         self.g = g
+        # kspace: None (finite differences, Eq. 1) or the kind of oracle.spectral's k-space advance
+        # ("spectral", "kt"), which carries its own form of the Sec. 3 correction
+        self.kspace = kspace
         self.filt = bool(filt)
         self.E = g.zeros()
         self.B = g.zeros()
@@ -208,9 +211,13 @@ class Sim:
             sp.xi = xi1
         if self.filt:
             filter_z(g, self.J)
-        if self.h is not None:
-            correct_j1(g, self.h, self.J)
-        field_advance(g, self.E, self.B, self.J)
+        if self.kspace is not None:
+            from . import spectral
+            spectral.advance(g, self.E, self.B, self.J, self.kspace)
+        else:
+            if self.h is not None:
+                correct_j1(g, self.h, self.J)
+            field_advance(g, self.E, self.B, self.J)
         for sp in self.species:
             sp.xi[:, 1] = np.mod(sp.xi[:, 1], g.nx)
             if g.ndim == 3:

@@ -1,0 +1,189 @@
+"""Pins of the k-space field advance (oracle/spectral.py): the spectral solver of Sec. 2.3 and the
+Sec. 3 operator [k]_1 = [k1]_t applied exactly in k space.
+
+* With the Yee symbol on every axis, and with the Appendix C symbol along z, the k-space step is
+  the finite-difference step of Eq. 1 (the C oracle, periodic along z) to round-off: this fixes
+  the staggering phases, the curl signs and the order of the half steps.
+* A single Fourier mode follows the leapfrog's closed form E_n = E_0 cos(n w dt) with
+  cos(w dt) = 1 - (dt kappa)^2 / 2 (kappa = k for the spectral solver); with [k1]_t along z the
+  phase velocity along z is exactly c (w = k1), the property Sec. 3 builds the operator for.
+* With particles (Esirkepov current) Gauss's law d-.E = rho is kept to round-off, and it drifts
+  when the k-space correction of the current is left out.
+* The stability limit of each solver: the mode at the limit neither grows nor decays."""
+import numpy as np
+import pytest
+
+from oracle import core as oc
+from oracle import spectral as ks
+
+TABLE1 = np.loadtxt(__file__.replace("test_oracle_spectral.py", "golden/table1_coefficients.txt"))
+
+
+def _grid(nd, C=(1.0,), periodic=True, shape=2):
+    if nd == 2:
+        return oc.Grid(2, 48, 12, 1, 0.5, 0.4, 0.45, 0.15, C=C, shape=shape, periodic_z=periodic)
+    return oc.Grid(3, 40, 10, 6, 0.5, 0.4, 0.45, 0.12, C=C, shape=shape, periodic_z=periodic)
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_yee_symbols_equal_finite_differences(nd):
+    g = _grid(nd)
+    rng = np.random.default_rng(3)
+    E, B, J = (rng.normal(size=g.fshape) for _ in range(3))
+    E1, B1 = E.copy(), B.copy()
+    oc.field_advance(g, E1, B1, J)
+    E2, B2 = E.copy(), B.copy()
+    ks.advance(g, E2, B2, J, "yee")
+    scale = max(np.abs(E1).max(), np.abs(B1).max())
+    assert np.abs(E2 - E1).max() < 1e-12 * scale
+    assert np.abs(B2 - B1).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_appendix_c_symbol_equals_finite_differences(nd):
+    """M = 16 Appendix C stencil along z (Table 1), J = 0 (the k-space step also scales the current,
+    which the FD oracle does by a separate truncated correction)."""
+    g = _grid(nd, C=TABLE1)
+    rng = np.random.default_rng(4)
+    E, B = rng.normal(size=g.fshape), rng.normal(size=g.fshape)
+    J = g.zeros()
+    E1, B1 = E.copy(), B.copy()
+    oc.field_advance(g, E1, B1, J)
+    E2, B2 = E.copy(), B.copy()
+    ks.advance(g, E2, B2, J, "custom", C=TABLE1)
+    scale = max(np.abs(E1).max(), np.abs(B1).max())
+    assert np.abs(E2 - E1).max() < 1e-12 * scale
+    assert np.abs(B2 - B1).max() < 1e-12 * scale
+
+
+def _mode_run(g, kind, axis, m, nsteps):
+    """E polarised across `axis` (E2 for a z mode, E1 for an x or y mode), varying as cos along
+    `axis` at the component's own staggered positions, B = 0; returns E_n / E_0 on that component
+    and the symbol kappa of the mode."""
+    E, B, J = g.zeros(), g.zeros(), g.zeros()
+    n = (g.nz, g.nx, g.ny)[axis]
+    h = (g.dz, g.dx, g.dy)[axis]
+    k = 2 * np.pi * m / (n * h)
+    comp = 1 if axis == 0 else 0
+    # positions of that component along the axis: E2 sits on z nodes; E1 sits on x and y nodes
+    pos = np.arange(n) * h
+    prof = np.cos(k * pos)
+    shape = [1, 1, 1]
+    shape[2 - axis] = n
+    E[comp] = np.broadcast_to(prof.reshape(shape), g.fshape[1:])
+    E0 = E[comp].copy()
+    for _ in range(nsteps):
+        ks.advance(g, E, B, J, kind)
+    kap = float(ks.axis_symbol(kind, axis, np.array([k]), g)[0])
+    return E[comp], E0, kap
+
+
+@pytest.mark.parametrize("kind,axis", [("spectral", 0), ("spectral", 1), ("kt", 1), ("yee", 0)])
+def test_single_mode_follows_leapfrog_closed_form(kind, axis):
+    g = _grid(2)
+    En, E0, kap = _mode_run(g, kind, axis, 5, 37)
+    w_dt = np.arccos(1.0 - 0.5 * (g.dt * kap) ** 2)
+    assert np.abs(En - np.cos(37 * w_dt) * E0).max() < 1e-11
+
+
+def test_spectral_mode_along_y_in_3d():
+    g = _grid(3)
+    En, E0, kap = _mode_run(g, "spectral", 2, 2, 25)
+    w_dt = np.arccos(1.0 - 0.5 * (g.dt * kap) ** 2)
+    assert abs(kap - 2 * np.pi * 2 / (g.ny * g.dy)) < 1e-12
+    assert np.abs(En - np.cos(25 * w_dt) * E0).max() < 1e-11
+
+
+@pytest.mark.parametrize("m", [1, 7, 20])
+def test_kt_operator_gives_phase_velocity_c_along_z(m):
+    """[k]_1 = [k1]_t: cos(w dt) = 1 - 2 sin^2(k1 dt/2) = cos(k1 dt), so w = k1 for every mode
+    (the numerical Cerenkov condition of Sec. 3 removed along z)."""
+    g = _grid(2)
+    En, E0, kap = _mode_run(g, "kt", 0, m, 40)
+    k1 = 2 * np.pi * m / (g.nz * g.dz)
+    assert np.abs(En - np.cos(40 * k1 * g.dt) * E0).max() < 1e-11
+    # the spectral and Yee operators do not have it
+    for other in ("spectral", "yee"):
+        Eo, _, _ = _mode_run(g, other, 0, m, 40)
+        assert np.abs(Eo - np.cos(40 * k1 * g.dt) * E0).max() > 1e-4
+
+
+def _particles(g, n, seed):
+    rng = np.random.default_rng(seed)
+    xi = np.zeros((n, 3))
+    xi[:, 0] = rng.uniform(0.35 * g.nz, 0.65 * g.nz, n)
+    xi[:, 1] = rng.uniform(0, g.nx, n)
+    if g.ndim == 3:
+        xi[:, 2] = rng.uniform(0, g.ny, n)
+    u = rng.normal(size=(n, 3)) * 1.5
+    return oc.Species(xi, u, -1.0, 1.0, 0.3)
+
+
+def _gauss_k(sim, kind):
+    r = sim.rho()
+    return ks.div_minus(sim.g, sim.E, kind) - r
+
+
+@pytest.mark.parametrize("nd,kind,shape", [(2, "spectral", 2), (2, "kt", 1), (3, "spectral", 1), (3, "kt", 2)])
+def test_gauss_law_kept_with_particles(nd, kind, shape):
+    g = _grid(nd, periodic=False, shape=shape)
+    sim = oc.Sim(g, [_particles(g, 40, 11 + nd)], kspace=kind)
+    G0 = _gauss_k(sim, kind)
+    rmax = np.abs(sim.rho()).max()
+    for _ in range(12):
+        sim.step()
+    assert len(sim.species[0].xi) == 40                      # nobody reached the z ends
+    G = _gauss_k(sim, kind)
+    assert np.abs(G - G0).max() < 1e-11 * rmax
+    assert np.abs(ks.div_plus(g, sim.B, kind)).max() < 1e-11 * max(np.abs(sim.B).max(), 1e-300)
+    assert np.abs(sim.E).max() > 1e-3 * rmax                 # the particles did radiate
+
+
+def test_gauss_law_drifts_without_the_current_scaling():
+    """The same run with the current passed in pre-divided by the ratio kappa_Yee / kappa (so that
+    the advance effectively uses the raw Esirkepov current): Gauss's law is no longer kept."""
+    g = _grid(2, periodic=False)
+    sp = _particles(g, 40, 13)
+    sim = oc.Sim(g, [sp], kspace="spectral")
+    G0 = _gauss_k(sim, "spectral")
+    rmax = np.abs(sim.rho()).max()
+    _, _, ratio = ks.operators(g, "spectral")
+    for _ in range(12):
+        g_ = sim.g
+        sim.J[:] = 0.0
+        for s in sim.species:
+            eb = oc.gather(g_, sim.E, sim.B, s.xi)
+            oc.boris(eb, s.u, s.q * g_.dt / (2.0 * s.m))
+            xi1 = oc.move(g_, s.xi, s.u)
+            oc.deposit(g_, s.xi, xi1, s.u, s.Q, sim.J)
+            s.xi = xi1
+        Jk = np.fft.rfftn(sim.J, axes=(1, 2, 3))
+        Jk = np.stack([Jk[c] / ratio[c] for c in range(3)])
+        J_raw_in = np.fft.irfftn(Jk, s=(g.ny, g.nx, g.nz), axes=(1, 2, 3))
+        ks.advance(g_, sim.E, sim.B, J_raw_in, "spectral")
+        for s in sim.species:
+            s.xi[:, 1] %= g_.nx
+    G = _gauss_k(sim, "spectral")
+    assert np.abs(G - G0).max() > 1e-4 * rmax
+
+
+@pytest.mark.parametrize("kind,nd", [("spectral", 2), ("spectral", 3), ("kt", 2), ("kt", 3)])
+def test_stability_limit(kind, nd):
+    """At dt slightly below the limit the fastest mode stays bounded; slightly above it grows."""
+    dz, dx, dy = 0.5, 0.4, 0.45
+    dtmax = ks.cfl_dt(nd, kind, dz, dx, dy)
+    if kind == "spectral":
+        perp = [dx] + ([dy] if nd == 3 else [])
+        assert abs(dtmax - 2.0 / np.sqrt(sum((np.pi / h) ** 2 for h in [dz] + perp))) < 1e-15
+    for f, grows in ((0.999, False), (1.01, True)):
+        ny = 8 if nd == 3 else 1
+        g = oc.Grid(nd, 16, 8, ny, dz, dx, dy, f * dtmax)
+        E, B, J = g.zeros(), g.zeros(), g.zeros()
+        # the checkerboard: Nyquist along every axis
+        iz, ix, iy = np.meshgrid(np.arange(g.nz), np.arange(g.nx), np.arange(g.ny), indexing="ij")
+        chk = ((-1.0) ** (iz + ix + iy)).transpose(2, 1, 0)
+        E[0], E[1], E[2] = chk, -chk, 0.5 * chk
+        for _ in range(400):
+            ks.advance(g, E, B, J, kind)
+        amp = np.abs(E).max()
+        assert (amp > 1e3) == grows, (f, amp)
