@@ -33,7 +33,7 @@ def test_traffic_follows_the_recorded_code_hash(bench, tmp_path, monkeypatch):
     src = tmp_path / "k.cu"
     src.write_text("__global__ void k(float* a) { a[0] = 1.f; }\n")
     md = tmp_path / "summary.md"
-    md.write_text(f"code_sha1: {bench.code_sha1(src.read_text())}\ntraffic_bytes_per_launch: 12345\n")
+    md.write_text(f"code_sha1: {bench.code_sha1(src.read_text())}\ntraffic_bytes_per_step: 12345\n")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setitem(bench.TRAFFIC_SOURCES, ("particles", 2), ("summary.md", "k.cu"))
     assert bench.captured_traffic("particles", 2) == 12345.0
