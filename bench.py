@@ -421,6 +421,44 @@ def run_beam_secondary(args, dev, wname_sel):
     return out
 
 
+def kspace_cases(args):
+    """The k-space field advance (Sec. 2.3 spectral solver, Sec. 3 [k]_1 = [k1]_t): 2D 8192 x 2048
+    and 3D 512 x 256 x 256 at 0.9 of each solver's stability limit.  One advance = 9 forward and 6
+    inverse FP32 transforms (cuFFT) and one update kernel over the modes; reported as
+    cell-updates/s and as the finite-difference solver's 60 B/cell-update over its time."""
+    import torch
+    from paper_1910_13529_gb300 import (PIC_SOLVER_KT, PIC_SOLVER_SPECTRAL, pic_cfl_dt_kspace, pic_timing,
+                                        pic_timing_read)
+    from paper_1910_13529_gb300.runtime import Simulation
+    dev = torch.device("cuda:0")
+    peak, kind = measured_peak()
+    grids = [("2d_8192x2048", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dy=0.02)),
+             ("3d_512x256x256", dict(ndim=3, nz=512, nx=256, ny=256, dz=0.02, dx=0.05, dy=0.05))]
+    out = {}
+    for gname, geo in grids:
+        for sname, code in (("spectral", PIC_SOLVER_SPECTRAL), ("kt", PIC_SOLVER_KT)):
+            dt = 0.9 * pic_cfl_dt_kspace(geo["ndim"], code, geo["dz"], geo["dx"], geo["dy"])
+            sim = Simulation(device="cuda:0", solver=sname, dt=dt, **geo)
+            gen = torch.Generator(device="cuda:0").manual_seed(1)
+            for t in (sim.E, sim.B, sim.J):
+                t.copy_(torch.randn(t.shape, device="cuda:0", generator=gen) * 1e-3)
+            sim.step(max(args.warmup, 3))
+            torch.cuda.synchronize(dev)
+            pic_timing(sim.h, 1)
+            K = max(args.steps, 20)
+            sim.step(K)
+            kms, kl = pic_timing_read(sim.h, sim.stream)
+            pic_timing(sim.h, 0)
+            cells = sim.nz * sim.nx * sim.ny
+            ms = float(kms["fields"]) / max(int(kl["fields"]), 1)
+            gbs = BYTES_PER_CELL_UPDATE * cells / (ms / 1e3) / 1e9
+            out[f"{gname}_{sname}"] = {"cell-updates/s": cells / (ms / 1e3), "ms_per_advance": ms,
+                                       "achieved_GBps_at_60B": gbs, "frac": gbs / peak, "peak_kind": kind,
+                                       "dt": dt}
+            sim.close()
+    return out
+
+
 def fields_cases(args, which=None):
     """Field advance alone on grids far above L2: 2D 8192 x 2048 (Yee and customised M = 16) and
     3D 512 x 256 x 256 (customised), cell-updates/s and the HBM fraction at 60 B/cell-update."""
@@ -676,6 +714,7 @@ def run_ours(args, rank, world, local_rank):
         fc, kf = fields_cases(args)
         secondary["field_advance_large_grids"] = fc
         secondary["batched_scan"] = batch_case(max(args.steps, 20), max(args.warmup, 3))
+        secondary["kspace_field_advance"] = kspace_cases(args)
         secondary["stencil_tuning"] = tuning_case()
     if rank == 0 and world == 1 and not args.no_cpu_baseline and nd == 3 and not args.small:
         model, ncores = host_cpu()

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpic.so")
 PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_CUDA, PIC_ERR_OOM, PIC_ERR_TIMEOUT, PIC_ERR_STATE, PIC_ERR_CAPACITY = range(8)
 STATUS_NAMES = ["PIC_OK", "PIC_ERR_ARG", "PIC_ERR_CFL", "PIC_ERR_CUDA", "PIC_ERR_OOM", "PIC_ERR_TIMEOUT",
                 "PIC_ERR_STATE", "PIC_ERR_CAPACITY"]
-PIC_SOLVER_YEE, PIC_SOLVER_CUSTOM = 0, 1
+PIC_SOLVER_YEE, PIC_SOLVER_CUSTOM, PIC_SOLVER_SPECTRAL, PIC_SOLVER_KT = 0, 1, 2, 3
 PIC_FILTER_NONE, PIC_FILTER_5PASS = 0, 1
 PIC_MAX_M, PIC_MAX_HLEN, PIC_MAX_SPECIES, PIC_DIAG_N = 16, 24, 4, 10
 PIC_STATIC_RHO_CELLS = 1 << 20
@@ -26,7 +26,7 @@ DIAG_KEYS = ["gauss_max", "gauss_rms", "rho_max", "field_energy", "kinetic", "co
 # exported symbols declared in include/pic.h
 EXPORTS = ["pic_create", "pic_destroy", "pic_last_error", "pic_fit_coefficients", "pic_fit_coefficients_b",
            "pic_correction_taps",
-           "pic_cfl_dt", "pic_cfl_dt_split", "pic_get_coefficients", "pic_get_coefficients_b", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
+           "pic_cfl_dt", "pic_cfl_dt_split", "pic_cfl_dt_kspace", "pic_get_coefficients", "pic_get_coefficients_b", "pic_bind_fields", "pic_bind_species", "pic_gather_push",
            "pic_deposit", "pic_field_advance", "pic_step", "pic_filter_current", "pic_sort", "pic_diag", "pic_rho", "pic_gauss",
            "pic_get_count", "pic_get_state", "pic_sync", "pic_timing", "pic_timing_read", "pic_gauss_static",
            "pic_batch_create", "pic_batch_instance", "pic_batch_step", "pic_batch_destroy", "pic_batch_get_tuning",
@@ -73,6 +73,8 @@ def _load():
         "pic_get_coefficients_b": ([vp, dp, ip], ctypes.c_int),
         "pic_cfl_dt_split": ([ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, dp,
                               ctypes.c_int, dp], ctypes.c_int),
+        "pic_cfl_dt_kspace": ([ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp],
+                              ctypes.c_int),
         "pic_bind_fields": ([vp, vp, vp, vp], ctypes.c_int),
         "pic_bind_species": ([vp, ctypes.c_int, vp, vp, vp, vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
                               ctypes.c_double, ctypes.c_double], ctypes.c_int),
@@ -184,6 +186,12 @@ def pic_cfl_dt_split(ndim, dz, dx, dy, CE, CB):
     out = ctypes.c_double()
     _check(lib.pic_cfl_dt_split(int(ndim), float(dz), float(dx), float(dy), _dptr(CE), _dptr(CB), M,
                                 ctypes.byref(out)))
+    return out.value
+
+
+def pic_cfl_dt_kspace(ndim, solver, dz, dx, dy=1.0):
+    out = ctypes.c_double()
+    _check(lib.pic_cfl_dt_kspace(int(ndim), int(solver), float(dz), float(dx), float(dy), ctypes.byref(out)))
     return out.value
 
 

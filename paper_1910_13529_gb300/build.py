@@ -12,14 +12,32 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libpic.so")
 SOURCES = ["pic_api.cu", "field_kernels.cu", "particle_kernels.cu", "diag_kernels.cu", "adjoint_kernels.cu",
-           "current_kernels.cu", "host_math.cpp"]
+           "current_kernels.cu", "kspace_kernels.cu", "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 
 
+def _cufft_dir():
+    """Directory of the toolkit's libcufft.so next to nvcc, or None (the k-space solvers are then
+    built as stubs that refuse)."""
+    import glob
+    import shutil
+    nvcc = shutil.which(NVCC)
+    if not nvcc:
+        return None
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    for d in [os.path.join(root, "lib64")] + sorted(glob.glob(os.path.join(root, "targets", "*", "lib"))):
+        if os.path.exists(os.path.join(d, "libcufft.so")) and os.path.exists(os.path.join(root, "include", "cufft.h")):
+            return d
+    return None
+
+
 def _flags():
-    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-                   "-I", os.path.join(HERE, "..", "include")]
+    f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+                "-I", os.path.join(HERE, "..", "include")]
+    if _cufft_dir():
+        f += ["-DPIC_HAVE_CUFFT"]
+    return f
 
 
 def _stale():
@@ -52,6 +70,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [NVCC] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+    fft = _cufft_dir()
+    if fft:
+        cmd += ["-L", fft, "-lcufft", "-Xlinker", "-rpath", "-Xlinker", fft]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")

@@ -181,4 +181,31 @@ double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M)
     return cfl_dt_split(ndim, dz, dx, dy, C, C, M);
 }
 
+// k-space solvers: the leapfrog is stable while (dt/2)^2 max_k sum_a [k]_a^2 <= 1, the maximum at
+// the Nyquist wavenumber of every axis.  Spectral: [k]_a = pi/h_a there.  [k1]_t along z (Yee
+// across): sin^2(pi dt/(2 dz)) + sum_perp (dt/h)^2 <= 1 with dt < dz, increasing in dt: bisection.
+double kspace_cfl_dt(int ndim, int kt, double dz, double dx, double dy) {
+    const double hp[2] = {dx, dy};
+    const int np = ndim == 3 ? 2 : 1;
+    if (!kt) {
+        double s = (M_PI / dz) * (M_PI / dz);
+        for (int a = 0; a < np; ++a) s += (M_PI / hp[a]) * (M_PI / hp[a]);
+        return 2.0 / std::sqrt(s);
+    }
+    auto f = [&](double dt) {
+        const double q = std::sin(0.5 * M_PI * dt / dz);
+        double v = q * q - 1.0;
+        for (int a = 0; a < np; ++a) v += (dt / hp[a]) * (dt / hp[a]);
+        return v;
+    };
+    double lo = 0.0, hi = dz;
+    if (f(hi) <= 0.0) return hi;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (f(mid) <= 0.0) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 }  // namespace pic

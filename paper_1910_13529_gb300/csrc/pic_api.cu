@@ -70,6 +70,7 @@ struct pic_t {
     float* adj_scratch = nullptr; // adjoint: B', E', W (7 N floats)
     double* static_rho = nullptr; // device address of g_static_rho on this handle's device
     int fa_variant = 0;           // field-advance tile variant (pic_autotune)
+    KSpaceState* ks = nullptr;    // k-space solvers: transforms, buffers and symbol tables
     double fa_ms[PIC_MAX_TILE_VARIANTS] = {0};   // measured time per variant (ms), 0 = not measured
 };
 
@@ -200,7 +201,12 @@ pic_status advance_fields(pic_t* h, const float* Ein, const float* Bin, float* E
     p.Eout = Eout;
     p.Bout = Bout;
     p.shift = shift;
-    {
+    if (h->ks) {
+        Scope sc(h, PIC_T_FIELDS, 1, s);
+        char kerr[256] = {0};
+        if (kspace_advance(h->ks, Ein, Bin, h->J, Eout, Bout, s, kerr, sizeof kerr))
+            return fail(h, PIC_ERR_CUDA, "%s", kerr);
+    } else {
         Scope sc(h, PIC_T_FIELDS, 1, s);
         CK(h, launch_field_advance(p, s, h->fa_variant), "field advance kernel");
     }
@@ -321,6 +327,14 @@ pic_status pic_cfl_dt_split(int ndim, double dz, double dx, double dy, const dou
     return PIC_OK;
 }
 
+pic_status pic_cfl_dt_kspace(int ndim, int solver, double dz, double dx, double dy, double* dt_out) {
+    if (!dt_out || (solver != PIC_SOLVER_SPECTRAL && solver != PIC_SOLVER_KT) || (ndim != 2 && ndim != 3) ||
+        !(dz > 0) || !(dx > 0) || (ndim == 3 && !(dy > 0)))
+        return PIC_ERR_ARG;
+    *dt_out = kspace_cfl_dt(ndim, solver == PIC_SOLVER_KT, dz, dx, dy);
+    return PIC_OK;
+}
+
 pic_status pic_cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M, double* dt_out) {
     if (!dt_out || !C || M < 1 || M > PIC_MAX_M || (ndim != 2 && ndim != 3) || !(dz > 0) || !(dx > 0) ||
         (ndim == 3 && !(dy > 0)))
@@ -342,8 +356,16 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     if (c.nz > 32768) return fail(nullptr, PIC_ERR_ARG, "nz above 32768");
     if (!(c.dz > 0) || !(c.dx > 0) || (c.ndim == 3 && !(c.dy > 0)) || !(c.dt > 0))
         return fail(nullptr, PIC_ERR_ARG, "cell sizes and dt must be positive");
-    if (c.solver != PIC_SOLVER_YEE && c.solver != PIC_SOLVER_CUSTOM)
+    if (c.solver != PIC_SOLVER_YEE && c.solver != PIC_SOLVER_CUSTOM && c.solver != PIC_SOLVER_SPECTRAL &&
+        c.solver != PIC_SOLVER_KT)
         return fail(nullptr, PIC_ERR_ARG, "unknown solver %d", c.solver);
+    const bool kspace = c.solver == PIC_SOLVER_SPECTRAL || c.solver == PIC_SOLVER_KT;
+    if (kspace) {
+        if (!kspace_available())
+            return fail(nullptr, PIC_ERR_ARG, "k-space solvers need cuFFT, which this build does not have");
+        if (c.moving_window) return fail(nullptr, PIC_ERR_ARG, "k-space solvers are periodic along z: no moving window");
+        if (c.coef_b) return fail(nullptr, PIC_ERR_ARG, "coef_b is for the customised solver");
+    }
     if (c.shape != 1 && c.shape != 2) return fail(nullptr, PIC_ERR_ARG, "shape must be 1 or 2");
     if (c.precision != 0 && c.precision != 32)
         return fail(nullptr, PIC_ERR_ARG, "precision %d: only FP32 (0 or 32) kernels are built", c.precision);
@@ -368,7 +390,8 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
         for (int l = 0; l < M; ++l) CB[l] = c.coef_b ? c.coef_b[l] : C[l];
     }
     const bool split = c.coef_b != nullptr;
-    double dtmax = cfl_dt_split(c.ndim, c.dz, c.dx, c.dy, C, CB, M);
+    double dtmax = kspace ? kspace_cfl_dt(c.ndim, c.solver == PIC_SOLVER_KT, c.dz, c.dx, c.ndim == 3 ? c.dy : 1.0)
+                          : cfl_dt_split(c.ndim, c.dz, c.dx, c.dy, C, CB, M);
     if (dtmax < 0.0) return fail(nullptr, PIC_ERR_ARG, "[k]_E1 [k]_B1 changes sign: unstable for every dt");
     if (c.dt > dtmax * (1.0 + 1e-12))
         return fail(nullptr, PIC_ERR_CFL, "dt = %.6g above the stability limit %.6g", c.dt, dtmax);
@@ -422,6 +445,15 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
         pic_destroy(h);
         return st;
     }
+    if (kspace) {
+        char kerr[256] = {0};
+        const int r = kspace_create(g, c.solver, c.dz, c.dx, h->cfg.dy, c.dt, &h->ks, kerr, sizeof kerr);
+        if (r) {
+            snprintf(g_create_err, sizeof g_create_err, "%s", kerr);
+            pic_destroy(h);
+            return r == 2 ? PIC_ERR_OOM : PIC_ERR_CUDA;
+        }
+    }
     cudaError_t e = cudaMemset(h->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->counts, 0, sizeof(int32_t) * PIC_MAX_SPECIES);
     if (e == cudaSuccess) {
@@ -444,6 +476,7 @@ pic_status pic_destroy(pic_t* h) {
                     h->cell_alt, h->off_alt, h->u_alt, h->id_alt};
     for (void* p : ptrs) dfree(p);
     dfree(h->adj_scratch);
+    kspace_destroy(h->ks);
     for (size_t i = 0; i < h->ev_a.size(); ++i) {
         cudaEventDestroy(h->ev_a[i]);
         cudaEventDestroy(h->ev_b[i]);
@@ -792,6 +825,7 @@ pic_status pic_adjoint_step(pic_t* h, const float* E, const float* B, const floa
                             double* grad, void* stream) {
     if (!h || !E || !B || !J || !aE || !aB || !grad) return PIC_ERR_ARG;
     if (h->split) return fail(h, PIC_ERR_ARG, "pic_adjoint_step needs one coefficient set (no coef_b)");
+    if (h->ks) return fail(h, PIC_ERR_ARG, "pic_adjoint_step: finite-difference solvers only");
     const long long N = h->g.ncell;
     if (!h->adj_scratch) {
         pic_status st = dalloc(h, &h->adj_scratch, 7 * N, "adjoint scratch");
@@ -827,6 +861,7 @@ pic_status pic_autotune(pic_t* h, void* stream) {
     if (!h) return PIC_ERR_ARG;
     pic_status st = need_fields(h);
     if (st) return st;
+    if (h->ks) return PIC_OK;           // one k-space advance: nothing to choose
     static std::vector<std::pair<std::vector<long long>, int>> cache;
     const int mclass = h->st.M <= 1 ? 1 : h->st.M <= 4 ? 4 : h->st.M <= 8 ? 8 : 16;
     std::vector<long long> key = {h->g.ndim, mclass, h->g.nz, h->g.nx, h->g.ny};
@@ -1134,6 +1169,10 @@ pic_status pic_batch_create(const pic_config* cfgs, int n, pic_batch_t** out) {
         if (cfgs[i].moving_window || cfgs[i].sort_every || cfgs[i].ndim != b->ndim) {
             pic_batch_destroy(b);
             return fail(nullptr, PIC_ERR_ARG, "batch instance %d: same ndim for all, no moving window, no sort", i);
+        }
+        if (cfgs[i].solver != PIC_SOLVER_YEE && cfgs[i].solver != PIC_SOLVER_CUSTOM) {
+            pic_batch_destroy(b);
+            return fail(nullptr, PIC_ERR_ARG, "batch instance %d: finite-difference solvers only", i);
         }
         pic_t* h = nullptr;
         pic_status st = pic_create(&cfgs[i], &h);

@@ -179,5 +179,17 @@ int correction_taps(const double* C, int M, int hlen, double* h);
 double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M);
 // with the E-side (CE) and B-side (CB) symbols: max of their product; -1 if the product is negative
 double cfl_dt_split(int ndim, double dz, double dx, double dy, const double* CE, const double* CB, int M);
+// k-space field advance (PIC_SOLVER_SPECTRAL, PIC_SOLVER_KT; kspace_kernels.cu).  Status codes:
+// 0 ok, 1 error (message in err), 2 device memory.
+struct KSpaceState;
+bool kspace_available();
+int kspace_create(const GridP& g, int solver, double dz, double dx, double dy, double dt, KSpaceState** out,
+                  char* err, size_t nerr);
+void kspace_destroy(KSpaceState* k);
+long long kspace_modes(const KSpaceState* k);
+int kspace_advance(KSpaceState* k, const float* Ein, const float* Bin, const float* J, float* Eout, float* Bout,
+                   cudaStream_t s, char* err, size_t nerr);
+// largest stable dt of the k-space solvers (kt = 0: spectral, 1: [k1]_t along z)
+double kspace_cfl_dt(int ndim, int kt, double dz, double dx, double dy);
 
 }  // namespace pic

@@ -36,14 +36,16 @@ def gpu_sim(grid, sps, coef=None, cap_extra=0, sort_every=0, ids=True):
 
 def oracle_sim(grid, sps, coef=None):
     nd = grid["ndim"]
-    C = (1.0,) if grid.get("solver", "yee") == "yee" else coef
+    solver = grid.get("solver", "yee")
+    kspace = solver if solver in ("spectral", "kt") else None
+    C = (1.0,) if solver in ("yee", "spectral", "kt") else coef
     Cb = grid.get("coef_b") if grid.get("solver", "yee") == "custom" else None
     g = oc.Grid(nd, grid["nz"], grid["nx"], grid.get("ny", 1), grid["dz"], grid["dx"],
                 grid.get("dy", grid["dx"]), grid["dt"], C=C, shape=grid.get("shape", 1), Cb=Cb)
     # Sec. 3 correction from the B-side coefficients (none when the B side is the Yee difference)
     CBeff = C if Cb is None else Cb
     yee_b = Cb is not None and np.allclose(np.asarray(Cb, dtype=np.float64), np.eye(1, len(Cb))[0], rtol=0, atol=0)
-    h = None if grid.get("solver", "yee") == "yee" or yee_b else fit.correction_kernel(CBeff, hlen=40)
+    h = None if solver != "custom" or yee_b else fit.correction_kernel(CBeff, hlen=40)
     species = [oc.Species(wl.xi_of(sp, nd), sp["u"].T.astype(np.float64), sp["q"], sp["m"], sp["w"],
                           ids=sp["ids"]) for sp in sps]
     inject = None
@@ -52,7 +54,7 @@ def oracle_sim(grid, sps, coef=None):
         inject = dict(species=grid["inject_species"], ppc=grid["inject_ppc"],
                       next_id=max(len(sp["iz"]) for sp in sps))
     return oc.Sim(g, species, h=h, moving_window=grid.get("moving_window", False), inject=inject,
-                  filt=grid.get("current_filter", False))
+                  filt=grid.get("current_filter", False), kspace=kspace)
 
 
 def field_error(sim, osim):

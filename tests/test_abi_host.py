@@ -141,3 +141,23 @@ def test_null_handle_calls_return_arg_error(P):
     assert P.lib.pic_step(None, 1, None) == P.PIC_ERR_ARG
     assert P.lib.pic_diag(None, None, None) == P.PIC_ERR_ARG
     assert P.lib.pic_destroy(None) == P.PIC_OK
+
+
+def test_kspace_limits_match_oracle_and_are_enforced(P):
+    """The k-space solvers (Sec. 2.3 spectral, Sec. 3 [k1]_t): the library's stability limits equal
+    the oracle's, dt above them and a moving window are refused before any device work."""
+    from oracle import spectral as ks
+    for nd, d in [(2, (0.05, 0.04, 0.04)), (3, (0.02, 0.05, 0.05))]:
+        for name, solver in (("spectral", P.PIC_SOLVER_SPECTRAL), ("kt", P.PIC_SOLVER_KT)):
+            a = P.pic_cfl_dt_kspace(nd, solver, *d)
+            assert a == pytest.approx(ks.cfl_dt(nd, name, *d), rel=1e-12)
+    with pytest.raises(P.PicError):
+        P.pic_cfl_dt_kspace(2, P.PIC_SOLVER_CUSTOM, 0.05, 0.05)
+    lim = P.pic_cfl_dt_kspace(2, P.PIC_SOLVER_SPECTRAL, 0.05, 0.05)
+    for kw, status in [(dict(solver="spectral", dt=1.01 * lim), P.PIC_ERR_CFL),
+                       (dict(solver="kt", dt=0.051), P.PIC_ERR_CFL),
+                       (dict(solver="spectral", dt=0.5 * lim, moving_window=True), P.PIC_ERR_ARG)]:
+        c, keep = _cfg(P, **kw)
+        with pytest.raises(P.PicError) as ei:
+            P.pic_create(c)
+        assert ei.value.status == status, kw

@@ -1,0 +1,113 @@
+"""GPU parity of the k-space field advance (PIC_SOLVER_SPECTRAL: Sec. 2.3, [k]_a = k_a;
+PIC_SOLVER_KT: Sec. 3, [k]_1 = [k1]_t along z in k space) against the FP64 oracle
+(oracle/spectral.py), through the C ABI.
+
+Tolerance as for the finite-difference solvers: 1e-5 of the largest |field| (positions 1e-5 cell,
+momenta 1e-5 of max |u|).  Grids with even and odd sizes (the r2c axis z and the full axes x, y),
+random fields with a random current, whole steps with two species, and Gauss's law with the
+solver's own divergence."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from oracle import core as oc  # noqa: E402
+from oracle import spectral as ks  # noqa: E402
+from paper_1910_13529_gb300 import workloads as wl  # noqa: E402
+
+from parity_util import field_error, field_rel_l2, gpu_particles, gpu_sim, oracle_sim, particle_errors  # noqa: E402
+
+TOL = 1e-5
+
+
+def kgrid(nd, nz, nx, ny, solver, shape=2, frac=0.9, d=(0.5, 0.4, 0.45)):
+    dt = frac * ks.cfl_dt(nd, solver, *d)
+    return dict(ndim=nd, nz=nz, nx=nx, ny=ny, dz=d[0], dx=d[1], dy=d[2], dt=dt, solver=solver, shape=shape)
+
+
+CASES = [
+    ("2d-spectral-even", 2, 96, 20, 1, "spectral"),
+    ("2d-kt-odd", 2, 95, 21, 1, "kt"),
+    ("3d-spectral-odd", 3, 49, 12, 9, "spectral"),
+    ("3d-kt-even", 3, 48, 10, 8, "kt"),
+]
+
+
+@pytest.mark.parametrize("name,nd,nz,nx,ny,solver", CASES)
+def test_kspace_field_advance(name, nd, nz, nx, ny, solver):
+    grid = kgrid(nd, nz, nx, ny, solver)
+    sim = gpu_sim(grid, [])
+    osim = oracle_sim(grid, [])
+    rng = np.random.default_rng(5)
+    for a, oa in ((sim.E, osim.E), (sim.B, osim.B), (sim.J, osim.J)):
+        v = rng.normal(size=oa.shape).astype(np.float32)
+        a.copy_(torch.from_numpy(v))
+        oa[:] = v
+    J0 = sim.J.clone()
+    for n in range(12):
+        sim.field_advance()
+        ks.advance(osim.g, osim.E, osim.B, osim.J, solver)
+        if n == 0:
+            assert field_error(sim, osim) < TOL
+            assert torch.equal(sim.J, J0)                 # the forward transforms keep their input
+    assert field_error(sim, osim) < TOL
+    assert field_rel_l2(sim, osim) < TOL
+    sim.close()
+
+
+@pytest.mark.parametrize("name,nd,nz,nx,ny,solver", CASES)
+def test_kspace_steps_with_particles(name, nd, nz, nx, ny, solver):
+    """Two species away from the z ends (the fields are periodic along z, the particles are not),
+    15 whole steps (fused gather + push + deposit, then the k-space advance)."""
+    grid = kgrid(nd, nz, nx, ny, solver, shape=2 if nd == 2 else 1)
+    m = int(0.35 * nz)
+    sps = [wl.random_particles(nd, nz, nx, ny, 1500, seed=11, u_scale=1.0, u_drift=(1.0, 0, 0), margin=m),
+           wl.random_particles(nd, nz, nx, ny, 400, seed=12, u_scale=0.2, margin=m, q=1.0, m=5.0, w=0.02)]
+    sim = gpu_sim(grid, sps)
+    osim = oracle_sim(grid, sps)
+    nsteps = 15
+    sim.step(nsteps)
+    for _ in range(nsteps):
+        osim.step()
+    assert field_error(sim, osim) < TOL
+    for s in range(2):
+        dx, du = particle_errors(sim, osim, s, nd)
+        assert dx < TOL and du < TOL, (s, dx, du)
+    # Gauss's law with the solver's own d-, from the GPU's fields and particles: the change of
+    # d-.E - rho over the run stays at FP32 round-off (E started at zero)
+    g = osim.g
+    rho, rho0 = np.zeros(g.fshape[1:]), np.zeros(g.fshape[1:])
+    for s, sp in enumerate(sps):
+        _, xi, _ = gpu_particles(sim, s, nd)
+        oc.rho(g, xi, sp["q"] * sp["w"], rho)
+        oc.rho(g, wl.xi_of(sp, nd), sp["q"] * sp["w"], rho0)
+    G = ks.div_minus(g, sim.E.double().cpu().numpy(), solver) - rho
+    assert np.abs(G + rho0).max() < 1e-4 * np.abs(rho0).max()
+    sim.close()
+
+
+def test_kt_vacuum_wave_moves_at_c():
+    """A z-directed vacuum wave on the GPU: with [k1]_t along z, E2 after n steps equals
+    cos(n k dt) E2(0) (phase velocity exactly c), against cos(n w dt) with w < k for the spectral
+    solver."""
+    grid = kgrid(2, 128, 8, 1, "kt", frac=0.7)
+    for solver, exact in (("kt", True), ("spectral", False)):
+        grid["solver"] = solver
+        sim = gpu_sim(grid, [])
+        k = 2 * np.pi * 9 / (grid["nz"] * grid["dz"])
+        prof = np.cos(k * np.arange(grid["nz"]) * grid["dz"]).astype(np.float32)
+        E = torch.zeros_like(sim.E)
+        E[1] = torch.from_numpy(np.broadcast_to(prof, (1, grid["nx"], grid["nz"])).copy())
+        sim.E.copy_(E)
+        sim.B.zero_()
+        sim.J.zero_()
+        sim.step(50)
+        got = sim.E[1].double().cpu().numpy()
+        want = np.cos(50 * k * grid["dt"]) * prof
+        err = np.abs(got - want).max()
+        assert (err < 1e-4) == exact, (solver, err)
+        sim.close()
