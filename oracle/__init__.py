@@ -14,6 +14,8 @@ Modules:
   fit.py        Appendix C coefficient fit, Sec. 3 current-correction kernel, CFL
   kspace.py     Sec. 2-3 k-space integrals: self-force (with and without the current
                 filter), kappa_r, on-axis E1, Appendix D closed forms
+  spectral.py   the k-space field advance (Sec. 2.3 spectral solver, Sec. 3 [k]_1 = [k1]_t
+                applied in k space) with numpy FFTs
 
 Pins (tests/test_oracle_*.py): plane-wave dispersion of Eq. wave, Gauss's law kept
 to round-off, Esirkepov continuity, Boris closed forms, the position update against
@@ -25,4 +27,7 @@ The 5-pass current filter (named, not defined, in the paper) is pinned through i
 symbol to the three filtered self-forces of Table 2.  The split axial operators ([k]_E1 != [k]_B1,
 Sec. 3) are pinned by the dispersion relation with the product of the two symbols, each side's
 operator, div curl = 0 and Gauss's law with the B-side correction (tests/test_oracle_split.py).
+The k-space advance is pinned to the finite-difference step (Yee and Appendix C symbols), the
+leapfrog's single-mode closed form, phase velocity c for [k1]_t, Gauss's law with its current
+scaling and its stability limits (tests/test_oracle_spectral.py).
 """
