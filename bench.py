@@ -58,10 +58,11 @@ def parse():
                     help="beam workloads with the 5-pass current filter along z (not the headline run)")
     ap.add_argument("--tile", type=int, default=None,
                     help="fields workload: force this field-advance tile variant instead of autotuning")
-    ap.add_argument("--workload", default="beam3d", choices=["beam2d", "beam3d", "batch", "fields"],
+    ap.add_argument("--workload", default="beam3d", choices=["beam2d", "beam3d", "batch", "fields", "kspace"],
                     help="beam3d: the headline 3D 512 x 256 x 256 beam in plasma; beam2d: the 2D 2048 x 512 "
                          "beam in plasma; batch: 256 independent single-particle runs, batched launch vs "
-                         "per-instance launches; fields: the field advance alone on grids above L2")
+                         "per-instance launches; fields: the field advance alone on grids above L2; kspace: "
+                         "the k-space (spectral, [k1]_t) field advance alone")
     return ap.parse_args()
 
 
@@ -781,8 +782,28 @@ def run_fields(args):
           "cases": out})
 
 
+def run_kspace(args):
+    """The k-space field advance alone (spectral and [k1]_t solvers, 2D 8192 x 2048 and 3D
+    512 x 256 x 256); the line's value is the 3D [k1]_t case."""
+    out = kspace_cases(args)
+    best = out["3d_512x256x256_kt"]
+    emit({"metric": METRIC, "value": best["cell-updates/s"], "unit": "cell-updates/s", "n_gpus": 1,
+          "steps": max(args.steps, 20), "warmup": max(args.warmup, 3), "ms_per_step": best["ms_per_advance"],
+          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+          "data": "synthetic (seeded random fields)",
+          "config": {"workload": "kspace_field_advance", "l2": "inputs larger than L2"},
+          "roofline": {"bound": "hbm", "kernel": "kspace_field_advance (cuFFT + update)",
+                       "achieved": best["achieved_GBps_at_60B"], "peak": measured_peak()[0], "unit": "GB/s",
+                       "frac": best["frac"], "peak_kind": best["peak_kind"], "traffic": None,
+                       "algorithmic_bytes_per_unit": 60},
+          "cases": out})
+
+
 def main():
     args = parse()
+    if args.workload == "kspace" and args.impl == "ours":
+        run_kspace(args)
+        return
     if args.workload == "batch" and args.impl == "ours":
         run_batch(args)
         return
