@@ -27,10 +27,12 @@ J' scales each component by kappa_Yee,a / kappa_a: the Esirkepov current obeys t
 equation with the Yee d-, the scaled one the continuity equation with this solver's d-, so
 Gauss's law d-.E = rho is kept (the k-space form of the Sec. 3 correction P^-1, here on every
 axis whose operator is not Yee).
+
+"psatd" is the analytic-time update of Appendix B (advance_psatd), on the same staggered fields.
 """
 import numpy as np
 
-KINDS = ("spectral", "kt", "yee", "custom")
+KINDS = ("spectral", "kt", "yee", "custom", "psatd")
 
 
 def yee_symbol(k, h):
@@ -97,7 +99,10 @@ def curl(d, F):
 
 
 def advance(g, E, B, J, kind, C=None):
-    """One step of Eq. 1 in k space, in place on the real arrays E, B (J is not modified)."""
+    """One step of Eq. 1 in k space, in place on the real arrays E, B (J is not modified); "psatd"
+    dispatches to advance_psatd."""
+    if kind == "psatd":
+        return advance_psatd(g, E, B, J)
     dp, dm, ratio = operators(g, kind, C)
     Ek, Bk, Jk = _fwd(E), _fwd(B), _fwd(J)
     Jk = np.stack([Jk[0] * ratio[0], Jk[1] * ratio[1], Jk[2] * ratio[2]])
@@ -122,11 +127,100 @@ def div_plus(g, F, kind, C=None):
     return np.fft.irfftn(dp[0] * Fk[0] + dp[1] * Fk[1] + dp[2] * Fk[2], s=(g.ny, g.nx, g.nz), axes=(0, 1, 2))
 
 
+# half-cell offsets of each component along (z, x, y): E1 z, E2 x, E3 y; B1 x y, B2 z y, B3 z x
+STAGGER_E = ((1, 0, 0), (0, 1, 0), (0, 0, 1))
+STAGGER_B = ((0, 1, 1), (1, 0, 1), (1, 1, 0))
+
+
+def _axes_k(g):
+    ks = [wavenumbers(g.nz, g.dz, True), wavenumbers(g.nx, g.dx, False),
+          wavenumbers(g.ny, g.dy, False) if g.ndim == 3 else np.zeros(1)]
+    shapes = [(1, 1, -1), (1, -1, 1), (-1, 1, 1)]
+    return [k.reshape(sh) for k, sh in zip(ks, shapes)]
+
+
+def _nyquist_mask(g):
+    """Modes on the Nyquist plane of an even axis (their half-cell phases are not real)."""
+    m = np.zeros((g.ny, g.nx, g.nz // 2 + 1), dtype=bool)
+    if g.nz % 2 == 0:
+        m[:, :, g.nz // 2] = True
+    if g.nx % 2 == 0:
+        m[:, g.nx // 2, :] = True
+    if g.ndim == 3 and g.ny % 2 == 0:
+        m[g.ny // 2, :, :] = True
+    return m
+
+
+def advance_psatd(g, E, B, J):
+    """One PSATD step (Appendix B, Eqs. B1-B2, with c = cos(k dt), s = sin(k dt), k = |k|):
+        E <- c E + i s khat x B - (s/k) J + (1 - c) khat (khat.E) + (s/k - dt) khat (khat.J)
+        B <- c B - i s khat x E + i (1 - c)/k khat x J           (both from the old E, B)
+    The formulas are for collocated fields: each staggered component is moved to the nodes by its
+    half-cell phase e^{-i k h/2} per staggered axis, updated, and moved back.  The current is scaled
+    per axis by [k]_Yee / k as for the spectral solver (so that the Esirkepov current obeys the
+    spectral continuity equation and Gauss's law i k.E = rho holds).  Modes on the Nyquist plane of
+    an even axis are removed (set to zero).  At k = 0: E <- E - dt J, B <- B."""
+    kz, kx, ky = _axes_k(g)
+    hs = (g.dz, g.dx, g.dy)
+    kv = (kz, kx, ky)
+    ph = [np.exp(-0.5j * kv[a] * hs[a]) for a in range(3)]
+    if g.ndim == 2:
+        ph[2] = np.ones(1).reshape(-1, 1, 1)
+
+    def colloc(Fk, stag, inv=False):
+        out = []
+        for c in range(3):
+            f = Fk[c]
+            for a in range(3):
+                if stag[c][a]:
+                    f = f * (np.conj(ph[a]) if inv else ph[a])
+            out.append(f)
+        return out
+
+    _, _, ratio = operators(g, "spectral")
+    Ek = colloc(_fwd(E), STAGGER_E)
+    Bk = colloc(_fwd(B), STAGGER_B)
+    Jraw = _fwd(J)
+    Jk = colloc(np.stack([Jraw[c] * ratio[c] for c in range(3)]), STAGGER_E)
+    kn = np.sqrt(kz ** 2 + kx ** 2 + ky ** 2)
+    zero = kn == 0.0
+    kn_safe = np.where(zero, 1.0, kn)
+    kh = [np.broadcast_to(k / kn_safe * (~zero), kn.shape) for k in (kz, kx, ky)]
+    C, S = np.cos(kn * g.dt), np.sin(kn * g.dt)
+    S_over_k = np.where(zero, g.dt, S / kn_safe)
+    omc_over_k = np.where(zero, 0.0, (1.0 - C) / kn_safe)
+
+    def cross(a, b):
+        return [a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]]
+
+    def dot(a, b):
+        return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]
+
+    kxB, kxE, kxJ = cross(kh, Bk), cross(kh, Ek), cross(kh, Jk)
+    kE, kJ = dot(kh, Ek), dot(kh, Jk)
+    En = [C * Ek[c] + 1j * S * kxB[c] - S_over_k * Jk[c] + (1.0 - C) * kh[c] * kE + (S_over_k - g.dt) * kh[c] * kJ
+          for c in range(3)]
+    Bn = [C * Bk[c] - 1j * S * kxE[c] + 1j * omc_over_k * kxJ[c] for c in range(3)]
+    nyq = _nyquist_mask(g)
+    En = [np.where(nyq, 0.0, f) for f in En]
+    Bn = [np.where(nyq, 0.0, f) for f in Bn]
+    E[:] = _inv(np.stack(colloc(En, STAGGER_E, inv=True)), g)
+    B[:] = _inv(np.stack(colloc(Bn, STAGGER_B, inv=True)), g)
+
+
+def div_spectral(g, F):
+    """i k.F of the collocated field (the divergence PSATD keeps), at the nodes; F staggered like E."""
+    return div_minus(g, F, "spectral")
+
+
 def cfl_dt(ndim, kind, dz, dx, dy=1.0):
     """Largest stable dt: the leapfrog needs (dt/2)^2 max_k sum_a kappa_a^2 <= 1.  For "kt" the z
     symbol depends on dt itself: sin^2(pi dt / (2 dz)) + sum_perp (dt/h)^2 ... <= 1 (dt < dz),
     solved by bisection."""
     perp = [dx] + ([dy] if ndim == 3 else [])
+    if kind == "psatd":
+        # unconditionally stable field update; the particle move is limited to one cell per step
+        return min([dz] + perp)
     if kind == "spectral":
         return 2.0 / np.sqrt(sum((np.pi / h) ** 2 for h in [dz] + perp))
     if kind == "kt":

@@ -187,3 +187,94 @@ def test_stability_limit(kind, nd):
             ks.advance(g, E, B, J, kind)
         amp = np.abs(E).max()
         assert (amp > 1e3) == grows, (f, amp)
+
+
+# ---------------------------------------------------------------- PSATD (Appendix B) ---
+
+def _odd_grid(nd, dt=0.3, shape=None):
+    if nd == 2:
+        return oc.Grid(2, 47, 13, 1, 0.5, 0.4, 0.45, dt, shape=2 if shape is None else shape)
+    return oc.Grid(3, 39, 11, 7, 0.5, 0.4, 0.45, dt, shape=1 if shape is None else shape)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_psatd_vacuum_modes_are_exact(axis):
+    """E_n = E_0 cos(n k dt) for a transverse mode (w = |k| in every direction), also at a dt
+    above the leapfrog limit of the spectral solver."""
+    g = oc.Grid(2, 48, 12, 1, 0.5, 0.4, 0.45, 0.9 * 0.4, shape=2, periodic_z=True)
+    assert g.dt > ks.cfl_dt(2, "spectral", g.dz, g.dx)
+    En, E0, kap = _mode_run(g, "psatd", axis, 5, 37)
+    k = 2 * np.pi * 5 / ((g.nz, g.nx)[axis] * (g.dz, g.dx)[axis])
+    assert np.abs(En - np.cos(37 * k * g.dt) * E0).max() < 1e-11
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_psatd_keeps_a_static_longitudinal_field(nd):
+    """E = -d+ phi (spectral forward difference of a random potential), B = 0, J = 0: unchanged."""
+    g = _odd_grid(nd)
+    rng = np.random.default_rng(8)
+    phi_k = np.fft.rfftn(rng.normal(size=(g.ny, g.nx, g.nz)))
+    dp, _, _ = ks.operators(g, "spectral")
+    E = np.stack([np.fft.irfftn(-dp[a] * phi_k, s=(g.ny, g.nx, g.nz), axes=(0, 1, 2)) for a in range(3)])
+    B, J = g.zeros(), g.zeros()
+    E0 = E.copy()
+    for _ in range(5):
+        ks.advance(g, E, B, J, "psatd")
+    assert np.abs(E - E0).max() < 1e-12 * np.abs(E0).max()
+    assert np.abs(B).max() < 1e-12 * np.abs(E0).max()
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_psatd_conserves_vacuum_energy_beyond_the_leapfrog_limit(nd):
+    g = _odd_grid(nd, dt=2.0 * ks.cfl_dt(nd, "spectral", 0.5, 0.4, 0.45))
+    rng = np.random.default_rng(9)
+    E, B, J = rng.normal(size=g.fshape), g.zeros(), g.zeros()
+    # remove the longitudinal part so that the whole field propagates
+    Ek = np.fft.rfftn(E, axes=(1, 2, 3))
+    dp, dm, _ = ks.operators(g, "spectral")
+    kz, kx, ky = ks._axes_k(g)
+    k2 = kz ** 2 + kx ** 2 + ky ** 2
+    div = sum(dm[a] * Ek[a] for a in range(3))
+    phi = np.where(k2 == 0, 0.0, div / np.where(k2 == 0, 1.0, -k2))
+    E = E - np.stack([np.fft.irfftn(dp[a] * phi, s=(g.ny, g.nx, g.nz), axes=(0, 1, 2)) for a in range(3)])
+    W0 = np.sum(E ** 2) + np.sum(B ** 2)
+    for _ in range(100):
+        ks.advance(g, E, B, J, "psatd")
+    assert abs(np.sum(E ** 2) + np.sum(B ** 2) - W0) < 1e-10 * W0
+    assert np.sum(B ** 2) > 0.1 * W0                            # the field did oscillate
+
+
+def test_psatd_approaches_the_spectral_leapfrog_as_dt_shrinks():
+    """With J = 0 PSATD is exact in time and the leapfrog's local error is O(dt^3): halving dt
+    divides the one-step difference by about 8 (smooth fields, low modes)."""
+    g = _odd_grid(2, dt=0.08)
+    kz, kx, _ = ks._axes_k(g)
+    rng = np.random.default_rng(10)
+    Ek = np.zeros((3,) + (g.ny, g.nx, g.nz // 2 + 1), dtype=complex)
+    low = (np.abs(kz) < 2.5) & (np.abs(kx) < 2.5)
+    for c in range(3):
+        Ek[c] = np.where(low, rng.normal(size=low.shape) + 1j * rng.normal(size=low.shape), 0.0)
+    E0 = np.fft.irfftn(Ek, s=(g.ny, g.nx, g.nz), axes=(1, 2, 3))
+    diffs = []
+    for dt in (0.08, 0.04):
+        g = _odd_grid(2, dt=dt)
+        Ea, Ba = E0.copy(), g.zeros()
+        Eb, Bb = E0.copy(), g.zeros()
+        ks.advance(g, Ea, Ba, g.zeros(), "psatd")
+        ks.advance(g, Eb, Bb, g.zeros(), "spectral")
+        diffs.append(max(np.abs(Ea - Eb).max(), np.abs(Ba - Bb).max()))
+    assert 6.0 < diffs[0] / diffs[1] < 10.0
+
+
+@pytest.mark.parametrize("nd,shape", [(2, 2), (3, 1)])
+def test_psatd_gauss_law_kept_with_particles(nd, shape):
+    g = _odd_grid(nd, shape=shape)
+    sim = oc.Sim(g, [_particles(g, 40, 21 + nd)], kspace="psatd")
+    G0 = _gauss_k(sim, "spectral")
+    rmax = np.abs(sim.rho()).max()
+    for _ in range(12):
+        sim.step()
+    assert len(sim.species[0].xi) == 40
+    G = _gauss_k(sim, "spectral")
+    assert np.abs(G - G0).max() < 1e-11 * rmax
+    assert np.abs(sim.E).max() > 1e-3 * rmax
