@@ -423,13 +423,14 @@ def run_beam_secondary(args, dev, wname_sel):
 
 
 def kspace_cases(args):
-    """The k-space field advance (Sec. 2.3 spectral solver, Sec. 3 [k]_1 = [k1]_t): 2D 8192 x 2048
-    and 3D 512 x 256 x 256 at 0.9 of each solver's stability limit.  One advance = 9 forward and 6
+    """The k-space field advance (Sec. 2.3 spectral solver, Sec. 3 [k]_1 = [k1]_t, Appendix B PSATD):
+    2D 8192 x 2048 and 3D 512 x 256 x 256 at 0.9 of each solver's stability limit (PSATD: of one
+    cell per step).  One advance = 9 forward and 6
     inverse FP32 transforms (cuFFT) and one update kernel over the modes; reported as
     cell-updates/s and as the finite-difference solver's 60 B/cell-update over its time."""
     import torch
-    from paper_1910_13529_gb300 import (PIC_SOLVER_KT, PIC_SOLVER_SPECTRAL, pic_cfl_dt_kspace, pic_timing,
-                                        pic_timing_read)
+    from paper_1910_13529_gb300 import (PIC_SOLVER_KT, PIC_SOLVER_PSATD, PIC_SOLVER_SPECTRAL, pic_cfl_dt_kspace,
+                                        pic_timing, pic_timing_read)
     from paper_1910_13529_gb300.runtime import Simulation
     dev = torch.device("cuda:0")
     peak, kind = measured_peak()
@@ -437,7 +438,7 @@ def kspace_cases(args):
              ("3d_512x256x256", dict(ndim=3, nz=512, nx=256, ny=256, dz=0.02, dx=0.05, dy=0.05))]
     out = {}
     for gname, geo in grids:
-        for sname, code in (("spectral", PIC_SOLVER_SPECTRAL), ("kt", PIC_SOLVER_KT)):
+        for sname, code in (("spectral", PIC_SOLVER_SPECTRAL), ("kt", PIC_SOLVER_KT), ("psatd", PIC_SOLVER_PSATD)):
             dt = 0.9 * pic_cfl_dt_kspace(geo["ndim"], code, geo["dz"], geo["dx"], geo["dy"])
             sim = Simulation(device="cuda:0", solver=sname, dt=dt, **geo)
             gen = torch.Generator(device="cuda:0").manual_seed(1)

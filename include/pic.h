@@ -70,7 +70,12 @@ typedef enum {
  *   PIC_SOLVER_SPECTRAL  [k]_a = k_a on every axis (Sec. 2.3);
  *   PIC_SOLVER_KT        [k]_1 = [k1]_t = (2/dt) sin(k1 dt/2) along z exactly, Yee across (the
  *                        operator Sec. 3 proposes, "advanced in k space"): vacuum waves along z
- *                        move at exactly c.
+ *                        move at exactly c;
+ *   PIC_SOLVER_PSATD     the analytic-time update of Appendix B (Eqs. B1-B2) with k = |k|: each
+ *                        staggered component is moved to the nodes by its half-cell phase, updated
+ *                        and moved back; modes on the Nyquist plane of an even axis are removed;
+ *                        vacuum waves move at exactly c in every direction, for any dt (the
+ *                        particle move still limits dt to one cell: dt <= min(dz, dx, dy)).
  * The forward difference from a node to the half-cell point above it has the symbol
  * e^{i k h/2} i [k]_a, the backward one e^{-i k h/2} i [k]_a; the current is scaled per axis by
  * [k]_Yee,a / [k]_a (the k-space Sec. 3 correction) so that Gauss's law with the solver's own
@@ -79,7 +84,7 @@ typedef enum {
  * pic_adjoint_step, no batches; pic_autotune does nothing; pic_diag/pic_gauss report the residual
  * of the finite-difference divergence, which these solvers do not keep (their own residual is
  * kept to round-off).  A build without cuFFT refuses them (PIC_ERR_ARG).                      */
-enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_CUSTOM = 1, PIC_SOLVER_SPECTRAL = 2, PIC_SOLVER_KT = 3 };
+enum { PIC_SOLVER_YEE = 0, PIC_SOLVER_CUSTOM = 1, PIC_SOLVER_SPECTRAL = 2, PIC_SOLVER_KT = 3, PIC_SOLVER_PSATD = 4 };
 
 /* Current filter along z (pic_config.current_filter).  The paper uses a "5 pass filter" with its
  * runs and with the self-forces of Table 2 and does not define it; PIC_FILTER_5PASS is the reading
@@ -116,7 +121,7 @@ typedef struct pic_config {
     int nz, nx, ny;         /* cells along z, x, y (ny ignored in 2D); nz, nx >= 2 */
     double dz, dx, dy;      /* cell sizes */
     double dt;              /* time step */
-    int solver;             /* PIC_SOLVER_YEE, _CUSTOM, _SPECTRAL or _KT (see above) */
+    int solver;             /* PIC_SOLVER_YEE, _CUSTOM, _SPECTRAL, _KT or _PSATD (see above) */
     int M;                  /* customised: number of coefficients C_1..C_M, 1 <= M <= PIC_MAX_M */
     const double* coef;     /* customised: host array of M coefficients; NULL fits them
                                (Appendix C, target [k1]_t = sin(k dt/2)/(dt/2), Sec. 3).  They
@@ -172,9 +177,10 @@ pic_status pic_cfl_dt(int ndim, double dz, double dx, double dy, const double* C
  * product [k]_E1 [k]_B1; PIC_ERR_ARG if that product changes sign (no stable dt).         */
 pic_status pic_cfl_dt_split(int ndim, double dz, double dx, double dy, const double* CE, const double* CB, int M,
                             double* dt_out);
-/* Largest stable dt of a k-space solver (PIC_SOLVER_SPECTRAL or PIC_SOLVER_KT): the leapfrog
+/* Largest stable dt of a k-space solver (PIC_SOLVER_SPECTRAL, _KT or _PSATD): the leapfrog
  * needs (dt/2)^2 max_k sum_a [k]_a^2 <= 1, reached at the Nyquist wavenumber of every axis;
- * spectral: dt = 2 / sqrt(sum_a (pi/h_a)^2); KT: sin^2(pi dt/(2 dz)) + sum_perp (dt/h)^2 = 1.
+ * spectral: dt = 2 / sqrt(sum_a (pi/h_a)^2); KT: sin^2(pi dt/(2 dz)) + sum_perp (dt/h)^2 = 1;
+ * PSATD: the field update is stable for any dt, the particle move limits it to min(dz, dx, dy).
  * PIC_ERR_ARG for another solver or non-positive sizes.                                   */
 pic_status pic_cfl_dt_kspace(int ndim, int solver, double dz, double dx, double dy, double* dt_out);
 /* Coefficients and taps a handle uses (C_out: PIC_MAX_M, h_out: 2*PIC_MAX_HLEN+1); C_out is

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libpic.so")
 PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_CUDA, PIC_ERR_OOM, PIC_ERR_TIMEOUT, PIC_ERR_STATE, PIC_ERR_CAPACITY = range(8)
 STATUS_NAMES = ["PIC_OK", "PIC_ERR_ARG", "PIC_ERR_CFL", "PIC_ERR_CUDA", "PIC_ERR_OOM", "PIC_ERR_TIMEOUT",
                 "PIC_ERR_STATE", "PIC_ERR_CAPACITY"]
-PIC_SOLVER_YEE, PIC_SOLVER_CUSTOM, PIC_SOLVER_SPECTRAL, PIC_SOLVER_KT = 0, 1, 2, 3
+PIC_SOLVER_YEE, PIC_SOLVER_CUSTOM, PIC_SOLVER_SPECTRAL, PIC_SOLVER_KT, PIC_SOLVER_PSATD = 0, 1, 2, 3, 4
 PIC_FILTER_NONE, PIC_FILTER_5PASS = 0, 1
 PIC_MAX_M, PIC_MAX_HLEN, PIC_MAX_SPECIES, PIC_DIAG_N = 16, 24, 4, 10
 PIC_STATIC_RHO_CELLS = 1 << 20

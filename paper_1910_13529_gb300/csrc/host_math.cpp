@@ -184,9 +184,15 @@ double cfl_dt(int ndim, double dz, double dx, double dy, const double* C, int M)
 // k-space solvers: the leapfrog is stable while (dt/2)^2 max_k sum_a [k]_a^2 <= 1, the maximum at
 // the Nyquist wavenumber of every axis.  Spectral: [k]_a = pi/h_a there.  [k1]_t along z (Yee
 // across): sin^2(pi dt/(2 dz)) + sum_perp (dt/h)^2 <= 1 with dt < dz, increasing in dt: bisection.
+// kt = 2 (PSATD): the analytic update is stable for any dt; the particle move allows one cell.
 double kspace_cfl_dt(int ndim, int kt, double dz, double dx, double dy) {
     const double hp[2] = {dx, dy};
     const int np = ndim == 3 ? 2 : 1;
+    if (kt == 2) {                         // PSATD: one cell per step for the particles
+        double h = std::fmin(dz, dx);
+        if (ndim == 3) h = std::fmin(h, dy);
+        return h;
+    }
     if (!kt) {
         double s = (M_PI / dz) * (M_PI / dz);
         for (int a = 0; a < np; ++a) s += (M_PI / hp[a]) * (M_PI / hp[a]);

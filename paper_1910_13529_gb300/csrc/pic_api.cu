@@ -328,10 +328,10 @@ pic_status pic_cfl_dt_split(int ndim, double dz, double dx, double dy, const dou
 }
 
 pic_status pic_cfl_dt_kspace(int ndim, int solver, double dz, double dx, double dy, double* dt_out) {
-    if (!dt_out || (solver != PIC_SOLVER_SPECTRAL && solver != PIC_SOLVER_KT) || (ndim != 2 && ndim != 3) ||
-        !(dz > 0) || !(dx > 0) || (ndim == 3 && !(dy > 0)))
+    if (!dt_out || (solver != PIC_SOLVER_SPECTRAL && solver != PIC_SOLVER_KT && solver != PIC_SOLVER_PSATD) ||
+        (ndim != 2 && ndim != 3) || !(dz > 0) || !(dx > 0) || (ndim == 3 && !(dy > 0)))
         return PIC_ERR_ARG;
-    *dt_out = kspace_cfl_dt(ndim, solver == PIC_SOLVER_KT, dz, dx, dy);
+    *dt_out = kspace_cfl_dt(ndim, solver == PIC_SOLVER_PSATD ? 2 : solver == PIC_SOLVER_KT ? 1 : 0, dz, dx, dy);
     return PIC_OK;
 }
 
@@ -357,9 +357,10 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
     if (!(c.dz > 0) || !(c.dx > 0) || (c.ndim == 3 && !(c.dy > 0)) || !(c.dt > 0))
         return fail(nullptr, PIC_ERR_ARG, "cell sizes and dt must be positive");
     if (c.solver != PIC_SOLVER_YEE && c.solver != PIC_SOLVER_CUSTOM && c.solver != PIC_SOLVER_SPECTRAL &&
-        c.solver != PIC_SOLVER_KT)
+        c.solver != PIC_SOLVER_KT && c.solver != PIC_SOLVER_PSATD)
         return fail(nullptr, PIC_ERR_ARG, "unknown solver %d", c.solver);
-    const bool kspace = c.solver == PIC_SOLVER_SPECTRAL || c.solver == PIC_SOLVER_KT;
+    const bool kspace = c.solver == PIC_SOLVER_SPECTRAL || c.solver == PIC_SOLVER_KT || c.solver == PIC_SOLVER_PSATD;
+    const int kkind = c.solver == PIC_SOLVER_PSATD ? 2 : c.solver == PIC_SOLVER_KT ? 1 : 0;
     if (kspace) {
         if (!kspace_available())
             return fail(nullptr, PIC_ERR_ARG, "k-space solvers need cuFFT, which this build does not have");
@@ -390,7 +391,7 @@ pic_status pic_create(const pic_config* cfg, pic_t** out) {
         for (int l = 0; l < M; ++l) CB[l] = c.coef_b ? c.coef_b[l] : C[l];
     }
     const bool split = c.coef_b != nullptr;
-    double dtmax = kspace ? kspace_cfl_dt(c.ndim, c.solver == PIC_SOLVER_KT, c.dz, c.dx, c.ndim == 3 ? c.dy : 1.0)
+    double dtmax = kspace ? kspace_cfl_dt(c.ndim, kkind, c.dz, c.dx, c.ndim == 3 ? c.dy : 1.0)
                           : cfl_dt_split(c.ndim, c.dz, c.dx, c.dy, C, CB, M);
     if (dtmax < 0.0) return fail(nullptr, PIC_ERR_ARG, "[k]_E1 [k]_B1 changes sign: unstable for every dt");
     if (c.dt > dtmax * (1.0 + 1e-12))

@@ -189,7 +189,7 @@ void kspace_destroy(KSpaceState* k);
 long long kspace_modes(const KSpaceState* k);
 int kspace_advance(KSpaceState* k, const float* Ein, const float* Bin, const float* J, float* Eout, float* Bout,
                    cudaStream_t s, char* err, size_t nerr);
-// largest stable dt of the k-space solvers (kt = 0: spectral, 1: [k1]_t along z)
+// largest stable dt of the k-space solvers (kt = 0: spectral, 1: [k1]_t along z, 2: PSATD)
 double kspace_cfl_dt(int ndim, int kt, double dz, double dx, double dy);
 
 }  // namespace pic

@@ -5,8 +5,8 @@ import ctypes
 import numpy as np
 import torch
 
-from . import (PIC_FILTER_5PASS, PIC_FILTER_NONE, PIC_SOLVER_CUSTOM, PIC_SOLVER_KT, PIC_SOLVER_SPECTRAL,
-               PIC_SOLVER_YEE, encode_cells, pic_batch_create, pic_batch_destroy,
+from . import (PIC_FILTER_5PASS, PIC_FILTER_NONE, PIC_SOLVER_CUSTOM, PIC_SOLVER_KT, PIC_SOLVER_PSATD,
+               PIC_SOLVER_SPECTRAL, PIC_SOLVER_YEE, encode_cells, pic_batch_create, pic_batch_destroy,
                pic_batch_instance, pic_batch_step, pic_bind_fields, pic_bind_species,
                pic_config, pic_create, pic_deposit, pic_destroy, pic_diag, pic_field_advance,
                pic_autotune, pic_gather_push, pic_gauss, pic_get_coefficients, pic_get_count, pic_get_state,
@@ -20,7 +20,7 @@ def make_config(ndim, nz, nx, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.5, solver="yee"
     c.ndim, c.nz, c.nx, c.ny = int(ndim), int(nz), int(nx), int(ny if ndim == 3 else 1)
     c.dz, c.dx, c.dy, c.dt = float(dz), float(dx), float(dy), float(dt)
     solvers = {"yee": PIC_SOLVER_YEE, "custom": PIC_SOLVER_CUSTOM, "spectral": PIC_SOLVER_SPECTRAL,
-               "kt": PIC_SOLVER_KT}
+               "kt": PIC_SOLVER_KT, "psatd": PIC_SOLVER_PSATD}
     if solver not in solvers:
         raise ValueError(f"solver {solver!r}: one of {sorted(solvers)}")
     c.solver = solvers[solver]

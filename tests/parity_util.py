@@ -37,8 +37,8 @@ def gpu_sim(grid, sps, coef=None, cap_extra=0, sort_every=0, ids=True):
 def oracle_sim(grid, sps, coef=None):
     nd = grid["ndim"]
     solver = grid.get("solver", "yee")
-    kspace = solver if solver in ("spectral", "kt") else None
-    C = (1.0,) if solver in ("yee", "spectral", "kt") else coef
+    kspace = solver if solver in ("spectral", "kt", "psatd") else None
+    C = (1.0,) if solver in ("yee", "spectral", "kt", "psatd") else coef
     Cb = grid.get("coef_b") if grid.get("solver", "yee") == "custom" else None
     g = oc.Grid(nd, grid["nz"], grid["nx"], grid.get("ny", 1), grid["dz"], grid["dx"],
                 grid.get("dy", grid["dx"]), grid["dt"], C=C, shape=grid.get("shape", 1), Cb=Cb)

@@ -153,10 +153,14 @@ def test_kspace_limits_match_oracle_and_are_enforced(P):
             assert a == pytest.approx(ks.cfl_dt(nd, name, *d), rel=1e-12)
     with pytest.raises(P.PicError):
         P.pic_cfl_dt_kspace(2, P.PIC_SOLVER_CUSTOM, 0.05, 0.05)
+    # PSATD: the field update is unconditionally stable, the particle move allows one cell
+    assert P.pic_cfl_dt_kspace(3, P.PIC_SOLVER_PSATD, 0.05, 0.04, 0.045) == 0.04
+    assert ks.cfl_dt(3, "psatd", 0.05, 0.04, 0.045) == 0.04
     lim = P.pic_cfl_dt_kspace(2, P.PIC_SOLVER_SPECTRAL, 0.05, 0.05)
     for kw, status in [(dict(solver="spectral", dt=1.01 * lim), P.PIC_ERR_CFL),
                        (dict(solver="kt", dt=0.051), P.PIC_ERR_CFL),
-                       (dict(solver="spectral", dt=0.5 * lim, moving_window=True), P.PIC_ERR_ARG)]:
+                       (dict(solver="spectral", dt=0.5 * lim, moving_window=True), P.PIC_ERR_ARG),
+                       (dict(solver="psatd", dt=0.051), P.PIC_ERR_CFL)]:
         c, keep = _cfg(P, **kw)
         with pytest.raises(P.PicError) as ei:
             P.pic_create(c)
