@@ -15,7 +15,7 @@ Modules:
   kspace.py     Sec. 2-3 k-space integrals: self-force (with and without the current
                 filter), kappa_r, on-axis E1, Appendix D closed forms
   spectral.py   the k-space field advance (Sec. 2.3 spectral solver, Sec. 3 [k]_1 = [k1]_t
-                applied in k space) with numpy FFTs
+                applied in k space, Appendix B PSATD) with numpy FFTs
 
 Pins (tests/test_oracle_*.py): plane-wave dispersion of Eq. wave, Gauss's law kept
 to round-off, Esirkepov continuity, Boris closed forms, the position update against
