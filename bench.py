@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true", help="headline only (profiling captures)")
     ap.add_argument("--small", action="store_true", help="reduced grid (profiling captures)")
-    ap.add_argument("--fields-case", default=None, choices=["2d_yee", "2d_custom16", "3d_custom16"],
+    ap.add_argument("--fields-case", default=None, choices=["2d_yee", "2d_custom16", "3d_custom16", "2d_pair16"],
                     help="fields workload: run this grid only (profiling captures)")
     ap.add_argument("--sort-every", type=int, default=20, help="steps between particle sorts")
     ap.add_argument("--filter", action="store_true",
@@ -462,10 +462,11 @@ def kspace_cases(args):
 
 
 def fields_cases(args, which=None):
-    """Field advance alone on grids far above L2: 2D 8192 x 2048 (Yee and customised M = 16) and
-    3D 512 x 256 x 256 (customised), cell-updates/s and the HBM fraction at 60 B/cell-update."""
+    """Field advance alone on grids far above L2: 2D 8192 x 2048 (Yee, customised M = 16 and the
+    Sec. 3 split pair) and 3D 512 x 256 x 256 (customised), cell-updates/s and the HBM fraction at
+    60 B/cell-update."""
     import torch
-    from paper_1910_13529_gb300 import pic_get_tuning, pic_set_tuning, pic_timing, pic_timing_read
+    from paper_1910_13529_gb300 import pic_fit_coefficients_b, pic_get_tuning, pic_set_tuning, pic_timing, pic_timing_read
     from paper_1910_13529_gb300 import workloads as wl
     from paper_1910_13529_gb300.runtime import Simulation
     dev = torch.device("cuda:0")
@@ -474,7 +475,11 @@ def fields_cases(args, which=None):
              ("2d_8192x2048_custom16", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dt=wl.DT_BEAM_2D,
                                             solver="custom", M=16)),
              ("3d_512x256x256_custom16", dict(ndim=3, nz=512, nx=256, ny=256, dz=0.02, dx=0.05, dy=0.05,
-                                              dt=wl.DT_BEAM_3D, solver="custom", M=16))]
+                                              dt=wl.DT_BEAM_3D, solver="custom", M=16)),
+             # Sec. 3 split pair: Yee E side, B side fitted so that [k]_E1 [k]_B1 = [k1]_t^2
+             ("2d_8192x2048_pair16", dict(ndim=2, nz=8192, nx=2048, dz=0.02, dx=0.02, dt=wl.DT_BEAM_2D,
+                                          solver="custom", coef=[1.0],
+                                          coef_b=pic_fit_coefficients_b(0.02 / wl.DT_BEAM_2D, [1.0], M=16)))]
     if which:
         cases = [c for c in cases if c[0] == which]
     out = {}
@@ -770,7 +775,7 @@ def run_fields(args):
     tag = None
     if args.fields_case:
         tag = {"2d_yee": "2d_8192x2048_yee", "2d_custom16": "2d_8192x2048_custom16",
-               "3d_custom16": "3d_512x256x256_custom16"}[args.fields_case]
+               "3d_custom16": "3d_512x256x256_custom16", "2d_pair16": "2d_8192x2048_pair16"}[args.fields_case]
     out, K = fields_cases(args, tag)
     best = out.get("2d_8192x2048_custom16", next(iter(out.values())))
     emit({"metric": METRIC, "value": best["cell-updates/s"], "unit": "cell-updates/s", "n_gpus": 1,
