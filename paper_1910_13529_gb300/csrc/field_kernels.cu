@@ -679,10 +679,16 @@ __device__ __forceinline__ void march_bnew_store(const FieldP& p, const float* e
     const GridP& g = p.g;
     const long long N = g.ncell;
     const float hz = 0.5f * g.dt / g.dz, hx = 0.5f * g.dt / g.dx, hy = 0.5f * g.dt / g.dy;
+    // shifted 16-byte stores take the next group's first cell from the next lane: the rows of the
+    // tile are whole runs of lanes and every warp runs the loop the same number of times
+    static_assert(32 % NG == 0 && (TX * NG) % 32 == 0, "tile rows aligned to warps");
+    const bool vshift = vec && p.shift;
     for (int it = threadIdx.x; it < TX * NG; it += blockDim.x) {
         const int gi = it % NG, x = it / NG;
         const int z = 4 * gi, gz = z0 + z, gx = x0 + x;
-        if (gz >= g.nz || gx >= g.nx) continue;
+        const bool valid = gz < g.nz && gx < g.nx;
+        if (!valid && !vshift) continue;   // (the shifted path computes on every lane: the planes hold
+                                           // the whole tile, so the shared reads stay inside them)
         const int eo = (x + 1) * WE + z + T::H0;
         const int bo = (x + 1) * WB + z + T::H1;
         float d2[4], d3[4], E2[4], E3[4], E1[4], E1x[4], E3x[4], E1y[4], E2y[4];
@@ -712,6 +718,39 @@ __device__ __forceinline__ void march_bnew_store(const FieldP& p, const float* e
             *reinterpret_cast<float4*>(p.Bout + o) = make_float4(b0[0], b0[1], b0[2], b0[3]);
             *reinterpret_cast<float4*>(p.Bout + N + o) = make_float4(b1[0], b1[1], b1[2], b1[3]);
             *reinterpret_cast<float4*>(p.Bout + 2 * N + o) = make_float4(b2[0], b2[1], b2[2], b2[3]);
+            continue;
+        }
+        if (vshift) {
+            // window shift, nz % 4 == 0: output group [gz, gz + 4) takes cells gz + 1 .. gz + 4.  Cell
+            // gz + 4 is the next lane's first cell; at the front (gz + 4 == nz) it is the zeroed
+            // front column; for the last group of a tile row it belongs to the next tile, whose first
+            // lane stores it one cell down (this group's last output), so this lane stores three.
+            const unsigned full = 0xffffffffu;
+            float nx6[6] = {E1[0], E2[0], E3[0], b0[0], b1[0], b2[0]};
+#pragma unroll
+            for (int c = 0; c < 6; ++c) nx6[c] = __shfl_down_sync(full, nx6[c], 1);
+            if (!valid) continue;
+            float* dst[6] = {p.Eout + row, p.Eout + N + row, p.Eout + 2 * N + row,
+                             p.Bout + row, p.Bout + N + row, p.Bout + 2 * N + row};
+            const float* src[6] = {E1, E2, E3, b0, b1, b2};
+            const bool front = gz + 4 >= g.nz;
+            if (front || gi != NG - 1) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c)
+                    *reinterpret_cast<float4*>(dst[c] + gz) =
+                        make_float4(src[c][1], src[c][2], src[c][3], front ? 0.f : nx6[c]);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) {
+                    dst[c][gz] = src[c][1];
+                    dst[c][gz + 1] = src[c][2];
+                    dst[c][gz + 2] = src[c][3];
+                }
+            }
+            if (gi == 0 && gz > 0) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) dst[c][gz - 1] = src[c][0];
+            }
             continue;
         }
 #pragma unroll
