@@ -31,7 +31,8 @@ struct KSpaceState {
     long long nk = 0;          // modes: (nz/2 + 1) nx ny
     int nzk = 0;
     float2* buf = nullptr;     // E, B, J in k space: 9 nk complex values
-    float4* tab = nullptr;     // per axis and index: (d+ re, d+ im, [k]_Yee / [k], 0); z, then x, then y
+    float4* tab = nullptr;     // per axis and index, z then x then y: spectral/KT (d+ re, d+ im,
+                               // [k]_Yee / [k], 0); PSATD (cos(k h/2), sin(k h/2), k, ratio or -1)
 #ifdef PIC_HAVE_CUFFT
     cufftHandle r2c = 0, c2r = 0;
     bool have_r2c = false, have_c2r = false;
