@@ -278,3 +278,33 @@ def test_psatd_gauss_law_kept_with_particles(nd, shape):
     G = _gauss_k(sim, "spectral")
     assert np.abs(G - G0).max() < 1e-11 * rmax
     assert np.abs(sim.E).max() > 1e-3 * rmax
+
+
+@pytest.mark.parametrize("nd", [2, 3])
+def test_correction_taps_match_the_exact_kspace_ratio(nd):
+    """Two independent routes to the Sec. 3 correction: the finite-difference step after
+    J1 <- h * J1 with the truncated taps of 1/P (fit.correction_kernel, 40 per side) equals the
+    k-space step with the Appendix C symbol, whose current is scaled by [k]_Yee / [k]_1 = 1/P
+    exactly, up to the taps' truncation.  The oracle's correction treats the z ends as open (zero
+    outside), so the comparison is on the cells more than 40 + 3 M from both ends."""
+    from oracle import fit
+    if nd == 2:
+        g = oc.Grid(2, 256, 12, 1, 0.5, 0.4, 0.45, 0.15, C=TABLE1, shape=2, periodic_z=True)
+    else:
+        g = oc.Grid(3, 224, 10, 6, 0.5, 0.4, 0.45, 0.12, C=TABLE1, shape=1, periodic_z=True)
+    rng = np.random.default_rng(12)
+    E, B, J = (rng.normal(size=g.fshape) for _ in range(3))
+    E1, B1, J1 = E.copy(), B.copy(), J.copy()
+    oc.correct_j1(g, fit.correction_kernel(TABLE1, hlen=40), J1)
+    oc.field_advance(g, E1, B1, J1)
+    E2, B2 = E.copy(), B.copy()
+    ks.advance(g, E2, B2, J, "custom", C=TABLE1)
+    m = 40 + 3 * 16 + 2
+    inner = (Ellipsis, slice(m, g.nz - m))
+    scale = max(np.abs(E1).max(), np.abs(B1).max())
+    assert np.abs(E2[inner] - E1[inner]).max() < 1e-12 * scale
+    assert np.abs(B2[inner] - B1[inner]).max() < 1e-12 * scale
+    # without the correction the two differ at the level of the current itself
+    E3, B3 = E.copy(), B.copy()
+    oc.field_advance(g, E3, B3, J)
+    assert np.abs(E3[inner] - E2[inner]).max() > 1e-3 * scale
