@@ -308,3 +308,50 @@ def test_correction_taps_match_the_exact_kspace_ratio(nd):
     E3, B3 = E.copy(), B.copy()
     oc.field_advance(g, E3, B3, J)
     assert np.abs(E3[inner] - E2[inner]).max() > 1e-3 * scale
+
+
+def psatd_b4_mode(g, m1, m2, beta):
+    """Appendix B, Eq. B4: the fields of a charge mode rho~ = 1 at k = (k1, k2) (2D) drifting along
+    x1 at beta (w = beta k1), with F = sin(k dt)/(k dt) (1 - cos w dt)/(cos w dt - cos k dt):
+        E1 = -i k1/k^2 + i k2^2/(k1 k^2) F,   E2 = -i (1 + F) k2/k^2,
+        B3 = -i k2/(k1 k^2) sin(w dt)/dt (1 - cos k dt)/(cos w dt - cos k dt);
+    the current that carries it, from the discrete continuity equation
+    (rho^{n+1} - rho^n)/dt + i k1 J1^{n+1/2} = 0 with J1^{n+1/2} = J1~ e^{-i w dt n}:
+    J1 = i (e^{-i w dt} - 1)/(k1 dt).  Returns the real staggered arrays of the mode at step 0
+    (J1 pre-divided by the current scaling [k]_Yee / k the advance applies) and at step 1."""
+    k1, k2 = 2 * np.pi * m1 / (g.nz * g.dz), 2 * np.pi * m2 / (g.nx * g.dx)
+    k = np.hypot(k1, k2)
+    w = beta * k1
+    ph = np.exp(-1j * w * g.dt)
+    den = np.cos(w * g.dt) - np.cos(k * g.dt)
+    F = np.sin(k * g.dt) / (k * g.dt) * (1 - np.cos(w * g.dt)) / den
+    E1 = -1j * k1 / k ** 2 + 1j * k2 ** 2 / (k1 * k ** 2) * F
+    E2 = -1j * (1 + F) * k2 / k ** 2
+    B3 = -1j * k2 / (k1 * k ** 2) * np.sin(w * g.dt) / g.dt * (1 - np.cos(k * g.dt)) / den
+    J1 = 1j * (ph - 1) / (k1 * g.dt) / ((2 / g.dz * np.sin(k1 * g.dz / 2)) / k1)
+    Z, X = np.meshgrid(np.arange(g.nz) * g.dz, np.arange(g.nx) * g.dx)
+
+    def f(amp, sz, sx):
+        return np.real(amp * np.exp(1j * (k1 * (Z + sz * g.dz) + k2 * (X + sx * g.dx))))
+
+    def fields(t):
+        E, B = g.zeros(), g.zeros()
+        E[0, 0], E[1, 0], B[2, 0] = f(E1 * t, 0.5, 0), f(E2 * t, 0, 0.5), f(B3 * t, 0.5, 0.5)
+        return E, B
+
+    J = g.zeros()
+    J[0, 0] = f(J1, 0.5, 0)
+    E0, B0 = fields(1.0)
+    E1_, B1_ = fields(ph)
+    return E0, B0, J, E1_, B1_
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.9])
+def test_psatd_reproduces_the_drifting_charge_fields_of_appendix_b(beta):
+    """One PSATD step carries the Eq. B4 fields of a drifting charge mode to e^{-i w dt} times
+    themselves (kappa = dx1/dt = 4, r = 1, as in the paper's Fig. 6)."""
+    g = oc.Grid(2, 32, 16, 1, 1.0, 1.0, 1.0, 0.25, periodic_z=True)
+    E, B, J, E1, B1 = psatd_b4_mode(g, 3, 2, beta)
+    ks.advance(g, E, B, J, "psatd")
+    assert np.abs(E - E1).max() < 1e-12 * np.abs(E1).max()
+    assert np.abs(B - B1).max() < 1e-12 * np.abs(E1).max()
