@@ -162,3 +162,20 @@ def test_psatd_vacuum_waves_move_at_c_beyond_the_leapfrog_limit():
         want = np.cos(40 * k * grid["dt"]) * np.broadcast_to(prof.reshape(shape), got.shape)
         assert np.abs(got - want).max() < 1e-4, axis
         sim.close()
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.9])
+def test_psatd_drifting_charge_fields_of_appendix_b(beta):
+    """The GPU's PSATD step carries the Eq. B4 fields of a drifting charge mode (Appendix B) to
+    e^{-i w dt} times themselves, as the oracle does (test_oracle_spectral.psatd_b4_mode)."""
+    from test_oracle_spectral import psatd_b4_mode
+    g = oc.Grid(2, 32, 16, 1, 1.0, 1.0, 1.0, 0.25, periodic_z=True)
+    E, B, J, E1, B1 = psatd_b4_mode(g, 3, 2, beta)
+    sim = gpu_sim(dict(ndim=2, nz=32, nx=16, ny=1, dz=1.0, dx=1.0, dy=1.0, dt=0.25, solver="psatd", shape=1), [])
+    for t, a in ((sim.E, E), (sim.B, B), (sim.J, J)):
+        t.copy_(torch.from_numpy(a.astype(np.float32)))
+    sim.field_advance()
+    scale = np.abs(E1).max()
+    assert np.abs(sim.E.double().cpu().numpy() - E1).max() < TOL * scale
+    assert np.abs(sim.B.double().cpu().numpy() - B1).max() < TOL * scale
+    sim.close()
