@@ -1,0 +1,91 @@
+"""Pin of the finite-difference step against the paper's per-mode fields of a drifting charge
+(Sec. 2.1, Eq. EM): for a charge mode rho~ at k = (k1, k2) moving along x1 at beta (w = beta k1),
+with D = [w]_t^2 - [k]_E1 [k]_B1 - [k]_E2 [k]_B2,
+
+    E1 = -(i/[k]_B1) ([w]_t^2 - [k]_E1 [k]_B1)/D rho~,   E2 = i [k]_E2/D rho~,
+    B3 = i ([k]_E2/[k]_B1) [w]_t/D rho~,                 J1 = ([w]_t/[k]_B1) rho~ (continuity),
+
+E at integer and B at half-integer times.  The step here keeps B at integer times (two half
+steps), whose amplitude is then B3 cos(w dt/2).  One step of the oracle must carry these fields to
+e^{-i w dt} times themselves, for the Yee solver, the Appendix C stencil (Table 1, where the E1
+numerator nearly vanishes at beta = 1: the point of Sec. 3) and the split pair with a Yee E side
+and the B side fitted to [k1]_t^2 / [k]_Yee ([k]_E1 != [k]_B1)."""
+import numpy as np
+import pytest
+
+from oracle import core as oc
+from oracle import fit
+from oracle import spectral as ks
+
+TABLE1 = np.loadtxt(__file__.replace("test_oracle_em.py", "golden/table1_coefficients.txt"))
+
+
+def em_mode(g, CE, CB, m1, m2, beta):
+    """Real staggered arrays of the Eq. EM mode at step 0 (J at step 1/2) and at step 1."""
+    k1, k2 = 2 * np.pi * m1 / (g.nz * g.dz), 2 * np.pi * m2 / (g.nx * g.dx)
+    kE1 = float(ks.axis_symbol("custom", 0, np.array([k1]), g, C=CE)[0])
+    kB1 = float(ks.axis_symbol("custom", 0, np.array([k1]), g, C=CB)[0])
+    kE2 = kB2 = 2 / g.dx * np.sin(k2 * g.dx / 2)
+    w = beta * k1
+    wt = 2 / g.dt * np.sin(w * g.dt / 2)
+    D = wt ** 2 - kE1 * kB1 - kE2 * kB2
+    E1 = -1j / kB1 * (wt ** 2 - kE1 * kB1) / D
+    E2 = 1j * kE2 / D
+    B3 = 1j * kE2 / kB1 * wt / D * np.cos(w * g.dt / 2)
+    J1 = wt / kB1 * np.exp(-0.5j * w * g.dt)
+    Z, X = np.meshgrid(np.arange(g.nz) * g.dz, np.arange(g.nx) * g.dx)
+
+    def f(amp, sz, sx):
+        return np.real(amp * np.exp(1j * (k1 * (Z + sz * g.dz) + k2 * (X + sx * g.dx))))
+
+    def fields(t):
+        E, B = g.zeros(), g.zeros()
+        E[0, 0], E[1, 0], B[2, 0] = f(E1 * t, 0.5, 0), f(E2 * t, 0, 0.5), f(B3 * t, 0.5, 0.5)
+        return E, B
+
+    J = g.zeros()
+    J[0, 0] = f(J1, 0.5, 0)
+    E0, B0 = fields(1.0)
+    En, Bn = fields(np.exp(-1j * w * g.dt))
+    return E0, B0, J, En, Bn, abs(E1)
+
+
+SOLVERS = {"yee": ((1.0,), None), "appendix_c": (TABLE1, None), "pair": ((1.0,), "fit")}
+
+
+def _sets(name, dz, dt):
+    CE, CB = SOLVERS[name]
+    if CB == "fit":
+        CB = fit.fit_coefficients(dz / dt, M=16, CE=[1.0])
+    return np.asarray(CE, dtype=np.float64), (None if CB is None else np.asarray(CB, dtype=np.float64))
+
+
+@pytest.mark.parametrize("name", list(SOLVERS))
+@pytest.mark.parametrize("beta", [1.0, 0.9])
+def test_one_step_carries_the_eq_em_fields(name, beta):
+    dz = dx = 1.0
+    dt = 0.25
+    CE, CB = _sets(name, dz, dt)
+    g = oc.Grid(2, 64, 16, 1, dz, dx, dx, dt, C=CE, Cb=CB, periodic_z=True)
+    E, B, J, En, Bn, e1 = em_mode(g, CE, CE if CB is None else CB, 5, 2, beta)
+    oc.field_advance(g, E, B, J)
+    scale = np.abs(En).max()
+    assert np.abs(E - En).max() < 1e-12 * scale
+    assert np.abs(B - Bn).max() < 1e-12 * scale
+    if name == "appendix_c" and beta == 1.0:
+        assert e1 < 1e-6 * scale            # [w]_t^2 - [k]_E1 [k]_B1 ~ 0: E1 of the drifting charge vanishes
+    if name == "yee" and beta == 1.0:
+        assert e1 > 1e-2 * scale
+
+
+def test_open_z_interior_matches():
+    """With open z ends (the PIC runs) the same holds more than 3 M + 2 cells from both ends."""
+    dz = dx = 1.0
+    dt = 0.25
+    g = oc.Grid(2, 256, 16, 1, dz, dx, dx, dt, C=TABLE1)
+    E, B, J, En, Bn, _ = em_mode(g, TABLE1, TABLE1, 20, 2, 1.0)
+    oc.field_advance(g, E, B, J)
+    inner = (Ellipsis, slice(50, g.nz - 50))
+    scale = np.abs(En).max()
+    assert np.abs(E[inner] - En[inner]).max() < 1e-12 * scale
+    assert np.abs(B[inner] - Bn[inner]).max() < 1e-12 * scale
