@@ -89,3 +89,39 @@ def test_open_z_interior_matches():
     scale = np.abs(En).max()
     assert np.abs(E[inner] - En[inner]).max() < 1e-12 * scale
     assert np.abs(B[inner] - Bn[inner]).max() < 1e-12 * scale
+
+
+@pytest.mark.parametrize("kind", ["spectral", "kt"])
+@pytest.mark.parametrize("beta", [1.0, 0.9])
+def test_kspace_leapfrog_carries_the_eq_em_fields(kind, beta):
+    """The k-space leapfrog (oracle/spectral.py) with [k]_1 = k1 (Sec. 2.3) or [k1]_t (Sec. 3) and
+    [k]_2 = k2 or the Yee symbol: the same Eq. EM mode, its current given to the advance divided by
+    the scaling [k]_Yee / [k] that the advance applies.  For "kt" at beta = 1 the E1 numerator
+    [w]_t^2 - [k]_1^2 vanishes identically."""
+    g = oc.Grid(2, 64, 16, 1, 1.0, 1.0, 1.0, 0.25, periodic_z=True)
+    k1, k2 = 2 * np.pi * 5 / g.nz, 2 * np.pi * 2 / g.nx
+    kap1 = float(ks.axis_symbol(kind, 0, np.array([k1]), g)[0])
+    kap2 = float(ks.axis_symbol(kind, 1, np.array([k2]), g)[0])
+    w = beta * k1
+    wt = 2 / g.dt * np.sin(w * g.dt / 2)
+    D = wt ** 2 - kap1 ** 2 - kap2 ** 2
+    E1 = -1j / kap1 * (wt ** 2 - kap1 ** 2) / D
+    E2 = 1j * kap2 / D
+    B3 = 1j * kap2 / kap1 * wt / D * np.cos(w * g.dt / 2)
+    ratio1 = (2 * np.sin(k1 / 2)) / kap1
+    J1 = wt / kap1 * np.exp(-0.5j * w * g.dt) / ratio1
+    Z, X = np.meshgrid(np.arange(g.nz) * 1.0, np.arange(g.nx) * 1.0)
+
+    def f(amp, sz, sx):
+        return np.real(amp * np.exp(1j * (k1 * (Z + sz) + k2 * (X + sx))))
+
+    E, B, J = g.zeros(), g.zeros(), g.zeros()
+    E[0, 0], E[1, 0], B[2, 0], J[0, 0] = f(E1, .5, 0), f(E2, 0, .5), f(B3, .5, .5), f(J1, .5, 0)
+    ks.advance(g, E, B, J, kind)
+    ph = np.exp(-1j * w * g.dt)
+    scale = max(abs(E2), abs(B3))
+    assert np.abs(E[0, 0] - f(E1 * ph, .5, 0)).max() < 1e-12 * scale
+    assert np.abs(E[1, 0] - f(E2 * ph, 0, .5)).max() < 1e-12 * scale
+    assert np.abs(B[2, 0] - f(B3 * ph, .5, .5)).max() < 1e-12 * scale
+    if kind == "kt" and beta == 1.0:
+        assert abs(E1) < 1e-12 * scale
