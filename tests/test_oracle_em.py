@@ -125,3 +125,40 @@ def test_kspace_leapfrog_carries_the_eq_em_fields(kind, beta):
     assert np.abs(B[2, 0] - f(B3 * ph, .5, .5)).max() < 1e-12 * scale
     if kind == "kt" and beta == 1.0:
         assert abs(E1) < 1e-12 * scale
+
+
+@pytest.mark.parametrize("name", ["yee", "appendix_c"])
+def test_one_step_carries_the_eq_em_fields_in_3d(name):
+    """3D: the mode at k = (k1, k2, k3) adds E3 = i [k]_E3/D rho~ (at (i, j, k+1/2)) and
+    B2 = -i ([k]_E3/[k]_B1) [w]_t/D rho~ (at (i+1/2, j, k+1/2)); B1 = 0."""
+    dz, dx, dy, dt, beta = 1.0, 1.0, 1.2, 0.25, 0.95
+    C = (1.0,) if name == "yee" else TABLE1
+    g = oc.Grid(3, 64, 12, 10, dz, dx, dy, dt, C=C, periodic_z=True)
+    k1, k2, k3 = 2 * np.pi * 5 / (g.nz * dz), 2 * np.pi * 2 / (g.nx * dx), 2 * np.pi * 3 / (g.ny * dy)
+    kE1 = float(ks.axis_symbol("custom", 0, np.array([k1]), g, C=np.asarray(C, dtype=np.float64))[0])
+    kE2 = 2 / dx * np.sin(k2 * dx / 2)
+    kE3 = 2 / dy * np.sin(k3 * dy / 2)
+    w = beta * k1
+    wt = 2 / dt * np.sin(w * dt / 2)
+    D = wt ** 2 - kE1 ** 2 - kE2 ** 2 - kE3 ** 2
+    cw = np.cos(w * dt / 2)
+    amp = {"E1": -1j / kE1 * (wt ** 2 - kE1 ** 2) / D, "E2": 1j * kE2 / D, "E3": 1j * kE3 / D,
+           "B2": -1j * kE3 / kE1 * wt / D * cw, "B3": 1j * kE2 / kE1 * wt / D * cw,
+           "J1": wt / kE1 * np.exp(-0.5j * w * dt)}
+    stag = {"E1": (.5, 0, 0), "E2": (0, .5, 0), "E3": (0, 0, .5), "B2": (.5, 0, .5), "B3": (.5, .5, 0),
+            "J1": (.5, 0, 0)}
+    Y, X, Z = np.meshgrid(np.arange(g.ny) * dy, np.arange(g.nx) * dx, np.arange(g.nz) * dz, indexing="ij")
+
+    def f(key, t=1.0):
+        sz, sx, sy = stag[key]
+        return np.real(amp[key] * t * np.exp(1j * (k1 * (Z + sz * dz) + k2 * (X + sx * dx) + k3 * (Y + sy * dy))))
+
+    E, B, J = g.zeros(), g.zeros(), g.zeros()
+    E[0], E[1], E[2], B[1], B[2], J[0] = f("E1"), f("E2"), f("E3"), f("B2"), f("B3"), f("J1")
+    oc.field_advance(g, E, B, J)
+    ph = np.exp(-1j * w * dt)
+    want_E = np.stack([f("E1", ph), f("E2", ph), f("E3", ph)])
+    want_B = np.stack([np.zeros_like(Z), f("B2", ph), f("B3", ph)])
+    scale = max(np.abs(want_E).max(), np.abs(want_B).max())
+    assert np.abs(E - want_E).max() < 1e-12 * scale
+    assert np.abs(B - want_B).max() < 1e-12 * scale
