@@ -23,7 +23,8 @@
  *   ny = 1 when ndim == 2.  Staggering: E1 (i+1/2,j,k), E2 (i,j+1/2,k), E3 (i,j,k+1/2),
  *   B1 (i,j+1/2,k+1/2), B2 (i+1/2,j,k+1/2), B3 (i+1/2,j+1/2,k); J like E; rho at nodes.
  *   In 2D, E3 and J3 sit at nodes and B1 at (i,j+1/2), B2 at (i+1/2,j), B3 at (i+1/2,j+1/2).
- *   Fields are zero outside 0 <= i < nz ("open"/conducting z ends) and periodic in x, y.
+ *   Fields are zero outside 0 <= i < nz ("open"/conducting z ends) and periodic in x, y (the
+ *   k-space solvers, PIC_SOLVER_SPECTRAL, _KT and _PSATD, are periodic along z as well).
  *
  * Particle layout (per species, structure of arrays, capacity cap):
  *   int32 cell[cap]   guarded linear cell index (iz + 1) + (nz + 2) * (ix + nx * iy),
